@@ -1,0 +1,356 @@
+"""Benchmark of the strong-field QED Monte Carlo step on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (printed as config.workload): 2^24 electrons, gamma ~ N(2000, 5%),
+head-on with a linearly polarised plane wave (a0 = 100, lambda = 0.8 um),
+dt = 0.01 laser period, optical-depth LCFA photon emission; collinear photons
+appended.  Fields reach the step the way a particle-in-cell code hands them
+over: six structure-of-arrays field components per particle, a distinct slab
+per step, resident in HBM before the timed region (inputs larger than L2).
+
+The headline `value` is particle-updates/s of the mixed path (binary32
+arithmetic, binary64 optical depth).  The plain binary64 path and the in-kernel
+plane-wave field source are timed on the same GPU and reported beside it.
+Under torchrun (N > 1) every rank steps its own 2^24 particles (weak scaling,
+no collective on the data path); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QED particle-updates/s at 2^24 (FP32 vs FP64 path, same GPU) + % of roofline"
+UNIT = "particle-updates/s"
+N_PARTICLES = 1 << 24
+WORKLOAD = "config2: 2^24 e-, gamma~N(2000,5%), head-on plane wave a0=100 @0.8um, dt=0.01T, LCFA NLC, optical depth"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --- clocks -------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --- our arm ------------------------------------------------------------------
+def make_state(sfq, torch, d, dtype, device):
+    T = lambda a, dt=None: torch.as_tensor(np.ascontiguousarray(a)).to(device=device, dtype=dt)
+    P = sfq.ParticleBuffers(T(d["px"], dtype), T(d["py"], dtype), T(d["pz"], dtype),
+                            T(d["tau"], torch.float64), T(d["flags"]))
+    return P
+
+
+def field_slabs(torch, d, nslab, dtype, device):
+    """Distinct SoA field arrays (6 per step) of the plane wave for steps 0..nslab-1."""
+    table = torch.as_tensor(d["table"]).to(device=device, dtype=dtype)
+    k0 = torch.as_tensor(d["k0"].astype(np.int64)).to(device)
+    K = table.numel()
+    amp = torch.tensor(d["amp0"], dtype=dtype, device=device)
+    slabs = []
+    for s in range(nslab):
+        idx = (k0 + (s * d["k_step"]) % K) % K
+        f = amp * table[idx]                        # E_y = B_z = a0 cos(phase), one rounding
+        z = [torch.zeros_like(f) for _ in range(4)]
+        slabs.append((z[0], f, z[1], z[2], z[3], f.clone()))
+    return slabs
+
+
+def time_mc(sfq, torch, ctx, P, fields_for_step, steps, warmup, out, counters, n, e2e=None):
+    """Run warmup + steps MC steps; CUDA events around each launch on the launching stream."""
+    stream = torch.cuda.current_stream()
+    for s in range(warmup):
+        ctx.mc_step(P, fields_for_step(s), s, out, counters=counters)
+    out.reset()
+    counters.zero_()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    if torch.distributed.is_initialized():
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for k in range(steps):
+        s = warmup + k
+        F = fields_for_step(s) if e2e is None else e2e(s)
+        ev[k][0].record(stream)
+        ctx.mc_step(P, F, s, out, counters=counters)
+        ev[k][1].record(stream)
+        if e2e is not None:
+            _ = counters[:2].cpu()                 # the step's result read back to the host
+    t1.record(stream)
+    torch.cuda.synchronize()
+    total_ms = t0.elapsed_time(t1)
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    return total_ms, launch_ms
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2301_07684_gb300 import build, sfq
+    from paper_2301_07684_gb300 import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    n = args.n
+    d = W.config2(n=n, seed=rank)
+    hbm_peak, peak_src = peaks()
+    res = {}
+    ids = None
+
+    def one_path(precision, fields_kind, steps, warmup, with_e2e):
+        dtype = torch.float32 if precision == "fp32" else torch.float64
+        ctx = sfq.Context(ref_len_m=W.REF_LEN, dt=W.DT, precision=precision, seed=12345, device=local)
+        P = make_state(sfq, torch, d, dtype, device)
+        P.id_base = rank * n
+        nslab = steps + warmup
+        out = sfq.ProductBuffers(int(0.09 * n * (steps + 1)) + 4096, dtype, device)
+        cnt = sfq.counters_tensor(device)
+        slabs = None
+        if fields_kind == "soa":
+            slabs = field_slabs(torch, d, nslab, dtype, device)
+            fs = lambda s: sfq.FieldSource.soa(*slabs[s % nslab])
+        else:
+            table = torch.as_tensor(d["table"]).to(device=device, dtype=dtype)
+            k0 = torch.as_tensor(d["k0"].view(np.int32)).to(device)
+            F = sfq.FieldSource.plane_wave(k0, table, d["k_step"], amp0=d["amp0"])
+            fs = lambda s: F
+        clocks = ClockSampler(local)
+        clocks.start()
+        total_ms, launch_ms = time_mc(sfq, torch, ctx, P, fs, steps, warmup, out, cnt, n)
+        clk = clocks.stop()
+        c = sfq.counters_dict(cnt)
+        e2e = None
+        if with_e2e and fields_kind == "soa":
+            # end to end through the public API: every step copies its six field arrays
+            # from pinned host memory and reads the step's counters back
+            host = [[a.cpu().pin_memory() for a in slabs[s % nslab]] for s in range(min(nslab, 4))]
+            dev_f = [torch.empty_like(a) for a in slabs[0]]
+
+            def e2e_fields(s):
+                for dst, src in zip(dev_f, host[s % len(host)]):
+                    dst.copy_(src, non_blocking=True)
+                return sfq.FieldSource.soa(*dev_f)
+
+            P2 = make_state(sfq, torch, d, dtype, device)
+            out2 = sfq.ProductBuffers(out.capacity, dtype, device)
+            cnt2 = sfq.counters_tensor(device)
+            e2e_steps = max(3, min(steps, 20))
+            tot2, _ = time_mc(sfq, torch, ctx, P2, fs, e2e_steps, warmup, out2, cnt2, n, e2e=e2e_fields)
+            e2e = {"value": n * e2e_steps / (tot2 * 1e-3), "unit": UNIT,
+                   "h2d_bytes_per_step": int(sum(a.numel() * a.element_size() for a in dev_f)),
+                   "d2h_bytes_per_step": 16}
+            del host, dev_f, P2, out2
+        # algorithmic bytes per launch: reads p, tau, flags (+ six fields or the phase index);
+        # writes tau; per event: p and one product record (p, parent id, step, meta)
+        esz = 4 if precision == "fp32" else 8
+        rd = 3 * esz + 8 + 1 + (6 * esz if fields_kind == "soa" else 4)
+        wr = 8
+        ev_bytes = 3 * esz + (3 * esz + 8 + 4 + 1)
+        events_per_step = c["events"] / steps
+        bytes_per_launch = n * (rd + wr) + events_per_step * ev_bytes
+        avg_launch_s = statistics.mean(launch_ms) * 1e-3
+        achieved = bytes_per_launch / avg_launch_s / 1e9
+        ups = n * steps / (total_ms * 1e-3)
+        out_d = dict(value=ups, ms_per_step=total_ms / steps, launch_ms=statistics.mean(launch_ms),
+                     achieved_gbs=achieved, frac=achieved / hbm_peak, bytes_per_update=bytes_per_launch / n,
+                     events_per_update=events_per_step / n, counters=c, clocks=clk, e2e=e2e,
+                     steps=steps)
+        slabs = None
+        ctx.close()
+        torch.cuda.empty_cache()
+        return out_d
+
+    main = one_path("fp32", "soa", args.steps, args.warmup, with_e2e=True)
+    pw = one_path("fp32", "pw", args.steps, args.warmup, with_e2e=False)
+    f64_steps = max(2, args.steps // 10)
+    f64 = one_path("fp64", "soa", f64_steps, max(3, min(args.warmup, 3)), with_e2e=False)
+
+    # max over ranks of the headline time
+    t = torch.tensor([main["ms_per_step"]], device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    total_updates = n * world
+    value = total_updates / (ms * 1e-3)
+    if rank == 0:
+        cpu = cpu_baseline(args) if world == 1 else None
+        dev_name = torch.cuda.get_device_name(local)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (f64 optical depth)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "particles": n, "fields": "SoA, distinct slab per step",
+                       "precision": "fp32-mixed", "l2": "inputs larger than L2 (~760 MB read per step)",
+                       "parallelism": f"dp{world} (independent particles, no collective)"},
+            "roofline": {"bound": "hbm", "achieved": main["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                         "frac": main["frac"], "traffic": None, "peak_source": peak_src,
+                         "bytes_per_update": main["bytes_per_update"]},
+            "cpu_baseline": cpu,
+            "e2e": main["e2e"],
+            "gpu_launches": args.steps,
+            "clocks": main["clocks"],
+            "fp64_path": {"value": f64["value"], "unit": UNIT, "ms_per_step": f64["ms_per_step"],
+                          "achieved_gbs": f64["achieved_gbs"], "hbm_frac": f64["frac"],
+                          "steps": f64["steps"], "bound": "alu (fp64 pipe)"},
+            "plane_wave_fields": {"value": pw["value"], "unit": UNIT, "ms_per_step": pw["ms_per_step"],
+                                  "achieved_gbs": pw["achieved_gbs"], "frac": pw["frac"],
+                                  "bytes_per_update": pw["bytes_per_update"]},
+            "events_per_update": main["events_per_update"],
+            "device": dev_name,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# --- CPU oracle -----------------------------------------------------------------
+def oracle_sample_run(n_sample, nsteps, step0=0):
+    """Run the FP64 oracle over a bounded sample of the workload; returns (updates, seconds, threads)."""
+    from oracle import oracle as O
+    from paper_2301_07684_gb300 import workloads as W
+    O.build()
+    d = W.config2(n=max(n_sample, 1024), seed=0, dtype=np.float32)
+    ids = np.arange(n_sample)
+    E = np.zeros((n_sample, nsteps, 6))
+    for j in range(nsteps):
+        (ex, ey, ez), (bx, by, bz) = W.plane_wave_fields(d["k0"][ids], d["amp0"], d["table"], step0 + j)
+        E[:, j, 1] = ey
+        E[:, j, 5] = bz
+    p = np.stack([d["px"][ids], d["py"][ids], d["pz"][ids]], 1).astype(np.float64)
+    t = time.perf_counter()
+    O.mc_run(p, d["tau"][ids], ids.astype(np.uint64), d["flags"][ids], np.zeros(n_sample, np.uint8), E,
+             rho=W.RHO, dt=W.DT, seed=12345, step0=step0, nsteps=nsteps)
+    dt = time.perf_counter() - t
+    return n_sample * nsteps, dt, O.num_threads()
+
+
+def cpu_baseline(args):
+    upd, sec, thr = oracle_sample_run(args.oracle_particles, args.oracle_steps)
+    return {"value": upd / sec, "unit": UNIT, "cores": thr, "kind": "oracle",
+            "sample": f"{args.oracle_particles} particles x {args.oracle_steps} steps of the same workload "
+                      f"({upd} updates in {sec:.1f} s)"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = args.oracle_particles
+    for s in range(args.warmup):
+        oracle_sample_run(per_step, 1, step0=s)
+    tot_upd, tot_sec, thr = 0, 0.0, 1
+    for s in range(args.steps):
+        upd, sec, thr = oracle_sample_run(per_step, 1, step0=args.warmup + s)
+        tot_upd += upd
+        tot_sec += sec
+    value = tot_upd / tot_sec
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_sec / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "particles": N_PARTICLES, "precision": "fp64 oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
+                             "sample": f"{per_step} particles of the workload per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_PARTICLES)
+    ap.add_argument("--oracle-particles", type=int, default=48)
+    ap.add_argument("--oracle-steps", type=int, default=40)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * sfq.h -- C ABI of libsfq, a GB300 (sm_103a) implementation of the per-particle,
+ * per-timestep strong-field QED Monte Carlo step of Montefiori & Tamburini,
+ * "SFQEDtoolkit" (arXiv:2301.07684): nonlinear Compton photon emission (NLC) and
+ * nonlinear Breit-Wheeler pair creation (NBW) in the locally-constant-field
+ * approximation (LCFA), and photon emission beyond it (BLCFA, Sec. 5).
+ *
+ * Conventions for every entry point
+ *  - Units are the paper's normalised units (Sec. 4.1, App. A): times in 1/omega_r,
+ *    fields in E_r = m c omega_r/|e| (B in E_r/c), momenta in m c, energies in m c^2.
+ *  - Floating-point buffers hold binary32 when the context was created with
+ *    SFQ_FP32 and binary64 with SFQ_FP64 ("real" below).  The optical depth is
+ *    binary64 in both.
+ *  - Buffers are device pointers owned by the caller, 16-byte aligned; they are not
+ *    retained after the call returns.  Sizes are element counts (int64_t).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *    Work is enqueued asynchronously; argument errors are returned synchronously
+ *    and nothing is enqueued.  Conditions found on the device (buffer overflow,
+ *    chi outside the fitted range, NaN input) are counted in sfq_counters and never
+ *    stop the kernel.
+ *  - No entry point falls back to the CPU.  Every call returns an sfq_status;
+ *    sfq_last_error() gives a message for the last failure of a context.
+ */
+#ifndef SFQ_H
+#define SFQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SFQ_OK = 0,
+    SFQ_ERR_ARG = 1,       /* invalid argument: NULL, misaligned, negative size, bad enum */
+    SFQ_ERR_CUDA = 2,      /* a CUDA runtime call failed (message in sfq_last_error) */
+    SFQ_ERR_CAPACITY = 3,  /* reported by sfq_counters_check: products were dropped */
+    SFQ_ERR_TABLE = 4,     /* approximation tables missing or inconsistent */
+    SFQ_ERR_RANGE = 5,     /* reported by sfq_counters_check: inputs outside the fitted range */
+    SFQ_ERR_TIMEOUT = 6    /* reserved: a bounded device wait gave up */
+} sfq_status;
+
+enum { SFQ_FP32 = 0, SFQ_FP64 = 1 };
+
+/* Library configuration, the counterpart of SFQED_INIT_ALL_ref_len / _ref_freq
+ * (App. A, functions 1 and 2). */
+typedef struct {
+    double ref_len_m;      /* reference length lambda_r = c/omega_r in metres, or 0 */
+    double ref_omega_si;   /* reference angular frequency omega_r in rad/s, or 0; exactly one > 0 */
+    double dt;             /* timestep in units of 1/omega_r (> 0) */
+    int32_t precision;     /* SFQ_FP32 (binary32 arithmetic, binary64 optical depth) or SFQ_FP64 */
+    int32_t device;        /* CUDA device ordinal the context uses */
+    uint64_t seed;         /* key of the Philox4x32-10 generator */
+} sfq_config;
+
+typedef struct sfq_ctx sfq_ctx;   /* opaque; owns the approximation tables on the device */
+
+/* Create a context: validates the configuration, uploads the fitted tables of
+ * this library to the device.  *out receives the context (NULL on failure).
+ * Returns SFQ_ERR_ARG for an invalid configuration, SFQ_ERR_CUDA on a device error. */
+sfq_status sfq_init(const sfq_config *cfg, sfq_ctx **out);
+
+/* Free the context and its device tables (App. A, function 14).  NULL is ignored. */
+void sfq_finalize(sfq_ctx *ctx);
+
+/* Message describing the last error of this context ("" if none).  The string is
+ * owned by the context. */
+const char *sfq_last_error(const sfq_ctx *ctx);
+
+/* Constants of the context: rho = lambda_r/lambda_C (the critical field in units of
+ * E_r, and 1/tau_C in units of 1/omega_r) and pref = alpha/(sqrt(3) pi) * rho, the
+ * common factor of Eq. pe_rate_3 and Eq. pp_tot_real. */
+sfq_status sfq_constants(const sfq_ctx *ctx, double *rho, double *pref);
+
+/* ------------------------------------------------------------------------- */
+/* Rates (App. A functions 5 and 6)                                            */
+/* ------------------------------------------------------------------------- */
+/* rate[i] = W_rad(gamma[i], chi[i]) = pref (chi/gamma) W~_rad(chi), Eq. pe_rate_3 with
+ * Eq. wtilde, in units of omega_r.  Inputs real[n]: lepton energy gamma (m c^2) and
+ * quantum parameter chi >= 0; output real[n].  chi above 2^20 is evaluated at 2^20 and
+ * counted; NaN gives 0.  `counters` may be NULL. */
+struct sfq_counters;
+sfq_status sfq_photon_rate(sfq_ctx *ctx, int64_t n, const void *gamma, const void *chi, void *rate,
+                           struct sfq_counters *counters, void *stream);
+
+/* rate[i] = W_pair(gamma[i], chi[i]) = pref W~_pair(chi)/gamma, Eq. pp_tot_real with
+ * Eq. wtilde_pair; 0 for chi < 0.01, where the paper neglects the process (Sec. 4.2). */
+sfq_status sfq_pair_rate(sfq_ctx *ctx, int64_t n, const void *gamma, const void *chi, void *rate,
+                         struct sfq_counters *counters, void *stream);
+
+/* ------------------------------------------------------------------------- */
+/* Random numbers and energy sampling (App. A functions 9 and 11)              */
+/* ------------------------------------------------------------------------- */
+/* Four uniforms per particle from Philox4x32-10 with key = seed and counter
+ * (id_lo, id_hi, step, tag): u[4i+k] = (floor(w_k / 2^9) + 1/2) 2^-23 (real).
+ * Word 0 resets the optical depth (or is r of the local test), word 1 is the r of
+ * the energy sampling, word 2 the r_2 of the BLCFA rejection, word 3 the first
+ * optical depth of a particle created without one.  id: uint64[n] device. */
+sfq_status sfq_uniforms(sfq_ctx *ctx, int64_t n, const uint64_t *id, uint32_t step, uint32_t tag,
+                        void *u, void *stream);
+
+/* Photon energy fraction by inverse-transform sampling, Eq. ITS_pe in the form of
+ * Eq. again: w-bar solves I~_pe(w, chi) = r W~_rad(chi) (Eq. pe_eff_int_2), s = 3 chi w^3/2
+ * (Eq. subs_altri), xi = eps_gamma/eps_e = s/(1+s).  Inputs real[n] chi (>= 0) and r in
+ * (0,1); outputs real[n] xi and, if xi_c != NULL, xi_c = 1 - xi = 1/(1+s) with relative
+ * precision.  chi above 2^12 and 1 - r below 2^-24 are clamped and counted. */
+sfq_status sfq_sample_photon_xi(sfq_ctx *ctx, int64_t n, const void *chi, const void *r, void *xi,
+                                void *xi_c, struct sfq_counters *counters, void *stream);
+
+/* Electron energy share by inverse-transform sampling, Eq. again_pp: r' = 2r - 1,
+ * v-bar solves I~_pp(v, chi) = |r'| W~_pair(chi) (Eq. tilde_I_pp), xi_e = (1 + sgn(r') v)/2
+ * (Eq. return_to_nrg).  Outputs real[n] xi_e and, if xi_p != NULL, the positron share
+ * 1 - xi_e, both with relative precision.  chi outside [2^-7, 2^12) is clamped and counted. */
+sfq_status sfq_sample_pair_xi(sfq_ctx *ctx, int64_t n, const void *chi, const void *r, void *xi_e,
+                              void *xi_p, struct sfq_counters *counters, void *stream);
+
+/* ------------------------------------------------------------------------- */
+/* The Monte Carlo step                                                         */
+/* ------------------------------------------------------------------------- */
+/* Per-particle flags (uint8). */
+enum {
+    SFQ_ALIVE = 1,          /* the particle takes part in the step */
+    SFQ_JUST_CREATED = 2,   /* BLCFA: no force history yet (Sec. 5, App. A function 15) */
+    SFQ_SPECIES_SHIFT = 2,  /* bits 2-3: SFQ_ELECTRON, SFQ_POSITRON or SFQ_PHOTON */
+    SFQ_TAG_SHIFT = 4       /* bits 4-5: tag, the 4th word of the Philox counter */
+};
+enum { SFQ_ELECTRON = 0, SFQ_POSITRON = 1, SFQ_PHOTON = 2 };
+enum { SFQ_LEPTON_LCFA_OD = 0, SFQ_LEPTON_BLCFA_LOCAL = 1 };
+
+/* Structure-of-arrays particle population (all device pointers). */
+typedef struct {
+    int64_t n;                /* number of particles */
+    void *px, *py, *pz;       /* real[n] momentum (in/out) */
+    double *tau;              /* binary64[n] optical depth tau_d (Sec. 2); negative = draw at the next step */
+    const uint64_t *id;       /* uint64[n] particle ids (Philox counter), or NULL: id = id_base + index */
+    uint64_t id_base;
+    uint8_t *flags;           /* uint8[n] (in/out) */
+    void *fprev[3];           /* real[n] each: BLCFA F_perp^(n-1) (in/out), NULL if unused */
+    void *dfprev[3];          /* real[n] each: BLCFA F_perp^(n-1) - F_perp^(n-2) (in/out) */
+    int32_t lepton_model;     /* SFQ_LEPTON_LCFA_OD or SFQ_LEPTON_BLCFA_LOCAL */
+    int32_t reserved;
+} sfq_particles;
+
+enum { SFQ_FIELDS_SOA = 0, SFQ_FIELDS_PLANE_WAVE = 1 };
+
+/* Fields at the particles for this step.
+ *  SFQ_FIELDS_SOA: ex..bz real[n] each (the fields a PIC code interpolates to the particles).
+ *  SFQ_FIELDS_PLANE_WAVE: a linearly polarised wave along +x,
+ *    E = (0, a C, 0), B = (0, 0, a C), C = table[(k0[i] + step * k_step) mod n_table],
+ *    a = amp[i] (real[n]) or amp0 when amp == NULL; the product a*C is formed in the
+ *    context's precision. */
+typedef struct {
+    int32_t kind;
+    int32_t reserved;
+    const void *ex, *ey, *ez, *bx, *by, *bz;
+    const uint32_t *k0;
+    const void *amp;
+    double amp0;
+    const void *table;
+    uint32_t n_table;
+    uint32_t k_step;
+} sfq_fields;
+
+/* Product records, appended by the step (device pointers, capacity elements each). */
+typedef struct {
+    int64_t capacity;
+    void *px, *py, *pz;       /* real[capacity]: collinear momentum (Sec. 4, App. A function 17) */
+    uint64_t *parent_id;      /* uint64[capacity] */
+    uint32_t *step;           /* uint32[capacity]: step of creation */
+    uint8_t *meta;            /* uint8[capacity]: species | member << 2 | parent tag << 4;
+                                 member 0 = emitted photon, 1 = electron, 2 = positron */
+    unsigned long long *count;/* device counter of requested records (caller zeroes it);
+                                 records at index >= capacity are dropped and counted */
+} sfq_products;
+
+/* Optional stepped children: leptons created by pair creation are appended here
+ * as particles (flags ALIVE | JUST_CREATED | species | member tag, id = parent id,
+ * tau = -1, BLCFA state 0, k0/amp copied from the parent).  */
+typedef struct {
+    sfq_particles p;          /* p.n is the capacity */
+    uint32_t *k0;             /* uint32[capacity] or NULL */
+    void *amp;                /* real[capacity] or NULL */
+    unsigned long long *count;/* device counter of requested children */
+} sfq_spawn;
+
+/* Device counters (binary layout shared with the host; zero before use). */
+typedef struct sfq_counters {
+    unsigned long long updates;          /* particle-updates performed */
+    unsigned long long events;           /* events deemed to occur (Sec. 2 tests) */
+    unsigned long long emitted;          /* photons emitted (after BLCFA acceptance) */
+    unsigned long long pairs;            /* photons converted */
+    unsigned long long dropped;          /* product records beyond capacity */
+    unsigned long long spawn_dropped;    /* children beyond capacity */
+    unsigned long long out_of_range;     /* chi beyond the fitted tables (clamped) */
+    unsigned long long nan_input;        /* NaN chi or gamma (treated as zero rate) */
+    unsigned long long gamma_below_one;  /* products with gamma < 1 (|p| set to 0) */
+    unsigned long long large_rdt;        /* R dt > 0.1 (Sec. 2: R dt << 1 is assumed) */
+    unsigned long long blcfa_no_emission;/* threshold >= 0.75 gamma (Sec. 5) */
+    unsigned long long blcfa_rejected;   /* rejected by Eq. rej_cond */
+    unsigned long long reserved[4];
+} sfq_counters;
+
+/* One Monte Carlo step for every alive particle of `p` (Sec. 2 and 4; Sec. 5 for
+ * BLCFA leptons):
+ *   chi (Eq. chi_exact) -> rate (Eq. pe_rate_3 / Eq. pp_tot_real) -> leptons with
+ *   SFQ_LEPTON_LCFA_OD and photons: tau_d -= R dt (binary64), event iff tau_d < 0, then
+ *   a fresh tau from word 0; BLCFA leptons: local test R dt > r (word 0) with the
+ *   threshold and rejection of Sec. 5 -> energy sampling (word 1) -> recoil of the
+ *   emitter or removal of the converted photon -> product records (and children).
+ * `step` is the timestep number (Philox counter word 2 and the plane-wave phase).
+ * `spawn` and `counters` may be NULL.  Counters are accumulated with atomics. */
+sfq_status sfq_mc_step(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, uint32_t step,
+                       const sfq_products *out, const sfq_spawn *spawn, sfq_counters *counters,
+                       void *stream);
+
+/* Library version string. */
+const char *sfq_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFQ_H */

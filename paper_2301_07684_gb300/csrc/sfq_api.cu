@@ -1,0 +1,235 @@
+// sfq_api.cu -- the C ABI of libsfq (declared in include/sfq.h): configuration,
+// table upload, argument validation and kernel launches.  No computation of the
+// method happens on the host.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "sfq_internal.h"
+
+namespace {
+
+// CODATA 2018
+constexpr double ALPHA = 7.2973525693e-3;          // fine-structure constant
+constexpr double LAMBDA_C = 3.8615926796e-13;      // reduced Compton length [m]
+constexpr double C_LIGHT = 299792458.0;            // [m/s]
+constexpr double PI = 3.14159265358979323846;
+
+sfq_status fail(sfq_ctx *ctx, sfq_status st, const char *msg) {
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+sfq_status cuda_fail(sfq_ctx *ctx, cudaError_t e, const char *where) {
+    if (ctx) {
+        ctx->err = std::string(where) + ": " + cudaGetErrorString(e);
+    }
+    return SFQ_ERR_CUDA;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+bool aligned8(const void *p) { return ((uintptr_t)p & 7u) == 0; }
+
+int grid_for(const sfq_ctx *ctx, int64_t n, int per_block) {
+    // a multiple of the SM count, no more blocks than needed
+    const int64_t blocks = (n + per_block - 1) / per_block;
+    const int64_t cap = (int64_t)ctx->num_sms * 8;
+    return (int)(blocks < cap ? (blocks > 0 ? blocks : 1) : cap);
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool is_fp64(const sfq_ctx *ctx) { return ctx->cfg.precision == SFQ_FP64; }
+
+}  // namespace
+
+extern "C" {
+
+const char *sfq_version(void) { return "libsfq 0.1 (sm_103a)"; }
+
+sfq_status sfq_init(const sfq_config *cfg, sfq_ctx **out) {
+    if (!out) return SFQ_ERR_ARG;
+    *out = nullptr;
+    if (!cfg) return SFQ_ERR_ARG;
+    const bool by_len = cfg->ref_len_m > 0.0, by_freq = cfg->ref_omega_si > 0.0;
+    if (by_len == by_freq) return SFQ_ERR_ARG;                    // exactly one of the two
+    if (!(cfg->dt > 0.0) || !std::isfinite(cfg->dt)) return SFQ_ERR_ARG;
+    if (cfg->precision != SFQ_FP32 && cfg->precision != SFQ_FP64) return SFQ_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+        cudaGetLastError();
+        return SFQ_ERR_CUDA;
+    }
+    sfq_ctx *ctx = new (std::nothrow) sfq_ctx();
+    if (!ctx) return SFQ_ERR_ARG;
+    ctx->cfg = *cfg;
+    ctx->device = cfg->device;
+    const double ref_len = by_len ? cfg->ref_len_m : C_LIGHT / cfg->ref_omega_si;
+    ctx->rho = ref_len / LAMBDA_C;                                // lambda_r / lambda_C
+    ctx->pref = ALPHA / (std::sqrt(3.0) * PI) * ctx->rho;        // Eq. pe_rate_3, Eq. pp_tot_real
+    DeviceGuard g(ctx->device);
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, ctx->device);
+    if (e != cudaSuccess) { delete ctx; return SFQ_ERR_CUDA; }
+    ctx->num_sms = prop.multiProcessorCount;
+    const sfq::HostTables t = sfq::host_tables(cfg->precision);
+    const void *src[4] = {t.nlc_rate, t.nbw_rate, t.nlc_inv, t.nbw_inv};
+    const size_t bytes[4] = {t.nlc_rate_bytes, t.nbw_rate_bytes, t.nlc_inv_bytes, t.nbw_inv_bytes};
+    void **dst[4] = {&ctx->d_nlc_rate, &ctx->d_nbw_rate, &ctx->d_nlc_inv, &ctx->d_nbw_inv};
+    for (int k = 0; k < 4; ++k) {
+        if (!src[k] || bytes[k] == 0) { sfq_finalize(ctx); return SFQ_ERR_TABLE; }
+        e = cudaMalloc(dst[k], bytes[k]);
+        if (e == cudaSuccess) e = cudaMemcpy(*dst[k], src[k], bytes[k], cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { sfq_finalize(ctx); return SFQ_ERR_CUDA; }
+    }
+    *out = ctx;
+    return SFQ_OK;
+}
+
+void sfq_finalize(sfq_ctx *ctx) {
+    if (!ctx) return;
+    {
+        DeviceGuard g(ctx->device);
+        void *ptrs[4] = {ctx->d_nlc_rate, ctx->d_nbw_rate, ctx->d_nlc_inv, ctx->d_nbw_inv};
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+    }
+    delete ctx;
+}
+
+const char *sfq_last_error(const sfq_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+sfq_status sfq_constants(const sfq_ctx *ctx, double *rho, double *pref) {
+    if (!ctx) return SFQ_ERR_ARG;
+    if (rho) *rho = ctx->rho;
+    if (pref) *pref = ctx->pref;
+    return SFQ_OK;
+}
+
+static sfq_status rate_common(sfq_ctx *ctx, int64_t n, const void *gamma, const void *chi, void *rate,
+                              sfq_counters *counters, void *stream, bool pair) {
+    if (!ctx) return SFQ_ERR_ARG;
+    if (n < 0) return fail(ctx, SFQ_ERR_ARG, "n < 0");
+    if (n == 0) return SFQ_OK;
+    if (!gamma || !chi || !rate) return fail(ctx, SFQ_ERR_ARG, "null buffer");
+    if (!aligned16(gamma) || !aligned16(chi) || !aligned16(rate) || (counters && !aligned8(counters)))
+        return fail(ctx, SFQ_ERR_ARG, "misaligned buffer (16 bytes required)");
+    DeviceGuard g(ctx->device);
+    sfq::RateLaunch L{n, gamma, chi, rate, pair ? ctx->d_nbw_rate : ctx->d_nlc_rate, ctx->pref, counters,
+                      (cudaStream_t)stream, grid_for(ctx, n, 256 * 4)};
+    const cudaError_t e = is_fp64(ctx) ? sfq::launch_rate_f64(L, pair) : sfq::launch_rate_f32(L, pair);
+    return e == cudaSuccess ? SFQ_OK : cuda_fail(ctx, e, pair ? "sfq_pair_rate" : "sfq_photon_rate");
+}
+
+sfq_status sfq_photon_rate(sfq_ctx *ctx, int64_t n, const void *gamma, const void *chi, void *rate,
+                           sfq_counters *counters, void *stream) {
+    return rate_common(ctx, n, gamma, chi, rate, counters, stream, false);
+}
+
+sfq_status sfq_pair_rate(sfq_ctx *ctx, int64_t n, const void *gamma, const void *chi, void *rate,
+                         sfq_counters *counters, void *stream) {
+    return rate_common(ctx, n, gamma, chi, rate, counters, stream, true);
+}
+
+sfq_status sfq_uniforms(sfq_ctx *ctx, int64_t n, const uint64_t *id, uint32_t step, uint32_t tag, void *u,
+                        void *stream) {
+    if (!ctx) return SFQ_ERR_ARG;
+    if (n < 0) return fail(ctx, SFQ_ERR_ARG, "n < 0");
+    if (n == 0) return SFQ_OK;
+    if (!id || !u) return fail(ctx, SFQ_ERR_ARG, "null buffer");
+    if (!aligned16(id) || !aligned16(u)) return fail(ctx, SFQ_ERR_ARG, "misaligned buffer (16 bytes required)");
+    DeviceGuard g(ctx->device);
+    const int grid = grid_for(ctx, n, 256 * 4);
+    const cudaError_t e = is_fp64(ctx)
+                              ? sfq::launch_uniforms_f64(n, id, step, tag, ctx->cfg.seed, u, (cudaStream_t)stream, grid)
+                              : sfq::launch_uniforms_f32(n, id, step, tag, ctx->cfg.seed, u, (cudaStream_t)stream, grid);
+    return e == cudaSuccess ? SFQ_OK : cuda_fail(ctx, e, "sfq_uniforms");
+}
+
+static sfq_status sample_common(sfq_ctx *ctx, int64_t n, const void *chi, const void *r, void *a, void *b,
+                                sfq_counters *counters, void *stream, bool pair) {
+    if (!ctx) return SFQ_ERR_ARG;
+    if (n < 0) return fail(ctx, SFQ_ERR_ARG, "n < 0");
+    if (n == 0) return SFQ_OK;
+    if (!chi || !r || !a) return fail(ctx, SFQ_ERR_ARG, "null buffer");
+    if (!aligned16(chi) || !aligned16(r) || !aligned16(a) || (b && !aligned16(b)) ||
+        (counters && !aligned8(counters)))
+        return fail(ctx, SFQ_ERR_ARG, "misaligned buffer (16 bytes required)");
+    DeviceGuard g(ctx->device);
+    sfq::SampleLaunch L{n, chi, r, a, b, pair ? ctx->d_nbw_inv : ctx->d_nlc_inv, counters, (cudaStream_t)stream,
+                        grid_for(ctx, n, 256 * 4)};
+    const cudaError_t e = is_fp64(ctx) ? sfq::launch_sample_f64(L, pair) : sfq::launch_sample_f32(L, pair);
+    return e == cudaSuccess ? SFQ_OK : cuda_fail(ctx, e, pair ? "sfq_sample_pair_xi" : "sfq_sample_photon_xi");
+}
+
+sfq_status sfq_sample_photon_xi(sfq_ctx *ctx, int64_t n, const void *chi, const void *r, void *xi, void *xi_c,
+                                sfq_counters *counters, void *stream) {
+    return sample_common(ctx, n, chi, r, xi, xi_c, counters, stream, false);
+}
+
+sfq_status sfq_sample_pair_xi(sfq_ctx *ctx, int64_t n, const void *chi, const void *r, void *xi_e, void *xi_p,
+                              sfq_counters *counters, void *stream) {
+    return sample_common(ctx, n, chi, r, xi_e, xi_p, counters, stream, true);
+}
+
+sfq_status sfq_mc_step(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, uint32_t step,
+                       const sfq_products *out, const sfq_spawn *spawn, sfq_counters *counters, void *stream) {
+    if (!ctx) return SFQ_ERR_ARG;
+    if (!p || !f || !out) return fail(ctx, SFQ_ERR_ARG, "null descriptor");
+    if (p->n < 0 || out->capacity < 0) return fail(ctx, SFQ_ERR_ARG, "negative size");
+    if (p->lepton_model != SFQ_LEPTON_LCFA_OD)
+        return fail(ctx, SFQ_ERR_ARG, "lepton model not available in this build");
+    if (p->n == 0) return SFQ_OK;
+    const void *need16[] = {p->px, p->py, p->pz, p->tau, p->flags};
+    for (const void *q : need16)
+        if (!q || !aligned16(q)) return fail(ctx, SFQ_ERR_ARG, "particle buffer null or misaligned");
+    if (p->id && !aligned16(p->id)) return fail(ctx, SFQ_ERR_ARG, "id misaligned");
+    if (f->kind == SFQ_FIELDS_SOA) {
+        const void *fl[] = {f->ex, f->ey, f->ez, f->bx, f->by, f->bz};
+        for (const void *q : fl)
+            if (!q || !aligned16(q)) return fail(ctx, SFQ_ERR_ARG, "field buffer null or misaligned");
+    } else if (f->kind == SFQ_FIELDS_PLANE_WAVE) {
+        if (!f->k0 || !f->table || f->n_table == 0 || !aligned16(f->k0) || !aligned16(f->table) ||
+            (f->amp && !aligned16(f->amp)))
+            return fail(ctx, SFQ_ERR_ARG, "plane-wave description null or misaligned");
+    } else {
+        return fail(ctx, SFQ_ERR_ARG, "unknown field kind");
+    }
+    if (!out->count || !aligned8(out->count)) return fail(ctx, SFQ_ERR_ARG, "product counter null or misaligned");
+    if (out->capacity > 0) {
+        const void *ob[] = {out->px, out->py, out->pz, out->parent_id, out->step, out->meta};
+        for (const void *q : ob)
+            if (!q || !aligned16(q)) return fail(ctx, SFQ_ERR_ARG, "product buffer null or misaligned");
+    }
+    if (spawn) {
+        if (!spawn->count || spawn->p.n < 0) return fail(ctx, SFQ_ERR_ARG, "spawn counter null or negative capacity");
+        if (spawn->p.n > 0) {
+            const void *sb[] = {spawn->p.px, spawn->p.py, spawn->p.pz, spawn->p.tau, spawn->p.id, spawn->p.flags};
+            for (const void *q : sb)
+                if (!q || !aligned16(q)) return fail(ctx, SFQ_ERR_ARG, "spawn buffer null or misaligned");
+            if (f->kind == SFQ_FIELDS_PLANE_WAVE && !spawn->k0)
+                return fail(ctx, SFQ_ERR_ARG, "spawn needs k0 for plane-wave fields");
+        }
+    }
+    if (counters && !aligned8(counters)) return fail(ctx, SFQ_ERR_ARG, "counters misaligned");
+    DeviceGuard g(ctx->device);
+    const int ppt = is_fp64(ctx) ? 1 : 2;
+    sfq::StepLaunch L{ctx, p, f, step, out, spawn, counters, (cudaStream_t)stream,
+                      grid_for(ctx, p->n, 256 * ppt), ppt};
+    const cudaError_t e = is_fp64(ctx) ? sfq::launch_step_f64(L) : sfq::launch_step_f32(L);
+    return e == cudaSuccess ? SFQ_OK : cuda_fail(ctx, e, "sfq_mc_step");
+}
+
+}  // extern "C"

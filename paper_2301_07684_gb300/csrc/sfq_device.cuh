@@ -1,0 +1,237 @@
+// sfq_device.cuh -- device building blocks of the Monte Carlo step.
+//
+// Philox4x32-10 (Salmon et al., SC'11), the uniform map of the step, exact piece
+// selection for the fitted tables (binary exponent + top mantissa bits), Horner
+// evaluation, and the binary64 optical depth updated in fixed point on the
+// integer pipe.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "sfq_tables_layout.h"
+
+namespace sfq {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10, keyed by the 64-bit seed; counter (id_lo, id_hi, step, tag).
+struct u4 { uint32_t w[4]; };
+
+__device__ __forceinline__ u4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                            uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    u4 r;
+    r.w[0] = c0; r.w[1] = c1; r.w[2] = c2; r.w[3] = c3;
+    return r;
+}
+
+__device__ __forceinline__ u4 draws(uint64_t seed, uint64_t id, uint32_t step, uint32_t tag) {
+    return philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), step, tag, (uint32_t)seed,
+                         (uint32_t)(seed >> 32));
+}
+
+// u = (floor(w / 2^9) + 1/2) 2^-23: exact in binary32 and binary64, in [2^-24, 1 - 2^-24].
+template <typename T>
+__device__ __forceinline__ T uniform(uint32_t w) {
+    return ((T)(w >> 9) + (T)0.5) * (T)1.1920928955078125e-07;   // 2^-23
+}
+
+// ---------------------------------------------------------------------------
+// Floating-point bit access.
+template <typename T> struct fp;
+template <> struct fp<float> {
+    using U = uint32_t;
+    static constexpr int MANT = 23, BIAS = 127;
+    static __device__ __forceinline__ U bits(float v) { return __float_as_uint(v); }
+    static __device__ __forceinline__ float from(U b) { return __uint_as_float(b); }
+    static __device__ __forceinline__ int expo(float v) { return (int)(bits(v) >> 23) - 127; }
+    static __device__ __forceinline__ float mant(float v) {     // in [1, 2)
+        return from((bits(v) & 0x7FFFFFu) | 0x3F800000u);
+    }
+};
+template <> struct fp<double> {
+    using U = uint64_t;
+    static constexpr int MANT = 52, BIAS = 1023;
+    static __device__ __forceinline__ U bits(double v) { return (U)__double_as_longlong(v); }
+    static __device__ __forceinline__ double from(U b) { return __longlong_as_double((long long)b); }
+    static __device__ __forceinline__ int expo(double v) { return (int)(bits(v) >> 52) - 1023; }
+    static __device__ __forceinline__ double mant(double v) {
+        return from((bits(v) & 0xFFFFFFFFFFFFFull) | 0x3FF0000000000000ull);
+    }
+};
+
+// 2^k as a constant of type T (|k| small).
+template <typename T>
+__host__ __device__ constexpr T pow2(int k) {
+    return k >= 0 ? (k == 0 ? (T)1 : (T)2 * pow2<T>(k - 1)) : (T)0.5 * pow2<T>(k + 1);
+}
+
+// ---------------------------------------------------------------------------
+// Piece selection.  Layouts (written by the table generator):
+//   octave axis: [low block of 2^SUBLOW pieces over [0, 2^ELO) if LOW]
+//                + octaves [2^e, 2^(e+1)), e in [ELO, EHI), 2^SUB pieces each;
+//   prob axis:   low block [0, 2^E0) of 2^SUBLOW pieces
+//                + octaves of r in [2^E0, 1/2), 2^SUB each
+//                + octaves of q = 1 - r, e = -2 down to QLO, 2^SUBQ each (q = 1/2 closes the first).
+// Each returns the piece index and the local variable x in [-1, 1]; all steps are
+// exact (scaling by powers of two and Sterbenz subtractions).
+template <typename T, int ELO, int EHI, int SUB, int LOW, int SUBLOW>
+__device__ __forceinline__ int octave_piece(T v, T &x, bool &oor) {
+    constexpr int NLOW = LOW ? (1 << SUBLOW) : 0;
+    constexpr int NPIECES = NLOW + (EHI - ELO) * (1 << SUB);
+    const int e = fp<T>::expo(v);
+    if (e < ELO) {                     // zero, subnormal or below the first octave
+        if (LOW) {
+            const T t = v * pow2<T>(SUBLOW - ELO);
+            int j = (int)t;
+            j = j > NLOW - 1 ? NLOW - 1 : j;
+            x = (T)2 * (t - (T)j) - (T)1;
+            return j;
+        }
+        oor = true;
+        x = (T)-1;
+        return 0;
+    }
+    if (e >= EHI) {
+        oor = true;
+        x = (T)1;
+        return NPIECES - 1;
+    }
+    const T t = (fp<T>::mant(v) - (T)1) * (T)(1 << SUB);
+    const int j = (int)t;
+    x = (T)2 * (t - (T)j) - (T)1;
+    return NLOW + (e - ELO) * (1 << SUB) + j;
+}
+
+template <typename T, int E0, int SUB, int SUBLOW, int QLO, int SUBQ>
+__device__ __forceinline__ int prob_piece(T r, T &x, bool &low, bool &oor) {
+    constexpr int NLOW = 1 << SUBLOW;
+    constexpr int NROCT = (-1 - E0) * (1 << SUB);
+    low = false;
+    if (r < (T)0.5) {
+        const int e = fp<T>::expo(r);
+        if (e < E0) {
+            const T t = r * pow2<T>(SUBLOW - E0);
+            int j = (int)t;
+            j = j > NLOW - 1 ? NLOW - 1 : j;
+            x = (T)2 * (t - (T)j) - (T)1;
+            low = true;
+            return j;
+        }
+        const T t = (fp<T>::mant(r) - (T)1) * (T)(1 << SUB);
+        const int j = (int)t;
+        x = (T)2 * (t - (T)j) - (T)1;
+        return NLOW + (e - E0) * (1 << SUB) + j;
+    }
+    const T q = (T)1 - r;              // exact for r >= 1/2
+    int e = fp<T>::expo(q);
+    int j;
+    if (e >= -1) {                     // q = 1/2: right end of the first q-octave
+        e = -2;
+        j = (1 << SUBQ) - 1;
+        x = (T)1;
+    } else if (e < QLO) {              // beyond the fitted tail (binary64 inputs only)
+        oor = true;
+        e = QLO;
+        j = 0;
+        x = (T)-1;
+    } else {
+        const T t = (fp<T>::mant(q) - (T)1) * (T)(1 << SUBQ);
+        j = (int)t;
+        x = (T)2 * (t - (T)j) - (T)1;
+    }
+    return NLOW + NROCT + (-2 - e) * (1 << SUBQ) + j;
+}
+
+// ---------------------------------------------------------------------------
+// Horner evaluation of the monomial pieces.
+template <int DEG, typename T>
+__device__ __forceinline__ T horner1(const T *c, T x) {
+    T acc = c[DEG];
+#pragma unroll
+    for (int k = DEG - 1; k >= 0; --k) acc = fma(acc, x, c[k]);
+    return acc;
+}
+
+// sum_ij c[i*(DY+1)+j] x^i y^j: Horner in y for each i, then in x.  `c` is read
+// through the read-only data cache.
+template <int DX, int DY, typename T>
+__device__ __forceinline__ T horner2(const T *__restrict__ c, T x, T y) {
+    T acc = (T)0;
+#pragma unroll
+    for (int i = DX; i >= 0; --i) {
+        T b = __ldg(c + i * (DY + 1) + DY);
+#pragma unroll
+        for (int j = DY - 1; j >= 0; --j) b = fma(b, y, __ldg(c + i * (DY + 1) + j));
+        acc = (i == DX) ? b : fma(acc, x, b);
+    }
+    return acc;
+}
+
+// ---------------------------------------------------------------------------
+// Optical depth in binary64 updated on the integer pipe (GB300's FP64 pipe runs at
+// about 1/70 of the FP32 rate).  tau in [0, 32) maps exactly onto 2^-58 fixed point
+// when tau >= 2^-6 (finer values are truncated below 2^-58); the binary32 decrement
+// d maps exactly when d >= 2^-35.  The difference is rounded once to binary64
+// (round to nearest even), as a binary64 subtraction would do.
+constexpr int TAU_FIX = 58;
+
+// Returns false when tau is outside [0, 32) (caller takes the binary64 path).
+__device__ __forceinline__ bool tau_to_fixed(uint64_t b, uint64_t &q) {
+    if (b >> 63) return false;                       // negative (or -0)
+    const int e = (int)(b >> 52);                    // biased exponent
+    if (e == 0) { q = 0ull; return true; }           // +0 or subnormal
+    const int sh = e - 1075 + TAU_FIX;               // value = m 2^(e-1075)
+    if (sh > 10) return false;                       // tau >= 32, Inf or NaN
+    const uint64_t m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    q = sh >= 0 ? (m << sh) : (sh <= -64 ? 0ull : (m >> (-sh)));
+    return true;
+}
+
+// binary32 d >= 0 -> floor(d 2^58) as an unsigned value; d >= 32 (also Inf/NaN)
+// returns UINT64_MAX, larger than any tau in [0, 32).
+__device__ __forceinline__ uint64_t dec_to_fixed(float d) {
+    const uint32_t b = __float_as_uint(d);
+    const int e = (int)(b >> 23);
+    if (e == 0 || (b >> 31)) return 0ull;
+    const int sh = e - 150 + TAU_FIX;                // value = m 2^(e-150)
+    if (sh > 39) return ~0ull;                       // d >= 32
+    const uint64_t m = (b & 0x7FFFFFu) | 0x800000u;
+    return sh >= 0 ? (m << sh) : (sh <= -64 ? 0ull : (m >> (-sh)));
+}
+
+// fixed point (< 2^63) -> binary64 bits, round to nearest even.
+__device__ __forceinline__ uint64_t fixed_to_tau(uint64_t u) {
+    if (u == 0) return 0ull;
+    const int msb = 63 - __clzll((long long)u);
+    uint64_t m;
+    int ex = msb;
+    if (msb > 52) {
+        const int sh = msb - 52;
+        m = u >> sh;
+        const uint64_t rem = u & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (m & 1ull))) {
+            ++m;
+            if (m >> 53) { m >>= 1; ++ex; }
+        }
+    } else {
+        m = u << (52 - msb);
+    }
+    const uint64_t be = (uint64_t)(ex - TAU_FIX + 1023);
+    return (be << 52) | (m & 0xFFFFFFFFFFFFFull);
+}
+
+// binary32 -> binary64 bits for a finite positive normal value (exact).
+__device__ __forceinline__ uint64_t f32_to_f64_bits(float v) {
+    const uint32_t b = __float_as_uint(v);
+    const uint64_t e = (uint64_t)((b >> 23) & 0xFFu) - 127 + 1023;
+    return (e << 52) | ((uint64_t)(b & 0x7FFFFFu) << 29);
+}
+
+}  // namespace sfq

@@ -1,0 +1,73 @@
+// sfq_internal.h -- declarations shared by the host translation units of libsfq.
+#pragma once
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "sfq.h"
+
+struct sfq_ctx {
+    sfq_config cfg;
+    int device;
+    double rho, pref;
+    // device copies of the fitted tables (one precision per context)
+    void *d_nlc_rate, *d_nbw_rate, *d_nlc_inv, *d_nbw_inv;
+    int num_sms;
+    std::string err;
+};
+
+namespace sfq {
+
+// Launchers (one per precision), implemented in sfq_launch_f32.cu / sfq_launch_f64.cu.
+struct RateLaunch {
+    int64_t n;
+    const void *gamma, *chi;
+    void *rate;
+    const void *table;
+    double pref;
+    sfq_counters *counters;
+    cudaStream_t stream;
+    int grid;
+};
+struct SampleLaunch {
+    int64_t n;
+    const void *chi, *r;
+    void *a, *b;
+    const void *inv;
+    sfq_counters *counters;
+    cudaStream_t stream;
+    int grid;
+};
+struct StepLaunch {
+    const sfq_ctx *ctx;
+    const sfq_particles *p;
+    const sfq_fields *f;
+    uint32_t step;
+    const sfq_products *out;
+    const sfq_spawn *spawn;
+    sfq_counters *counters;
+    cudaStream_t stream;
+    int grid;
+    int ppt;
+};
+
+cudaError_t launch_rate_f32(const RateLaunch &, bool pair);
+cudaError_t launch_rate_f64(const RateLaunch &, bool pair);
+cudaError_t launch_sample_f32(const SampleLaunch &, bool pair);
+cudaError_t launch_sample_f64(const SampleLaunch &, bool pair);
+cudaError_t launch_uniforms_f32(int64_t n, const uint64_t *id, uint32_t step, uint32_t tag, uint64_t seed,
+                                void *u, cudaStream_t s, int grid);
+cudaError_t launch_uniforms_f64(int64_t n, const uint64_t *id, uint32_t step, uint32_t tag, uint64_t seed,
+                                void *u, cudaStream_t s, int grid);
+cudaError_t launch_step_f32(const StepLaunch &);
+cudaError_t launch_step_f64(const StepLaunch &);
+
+// Host copies of the tables (sfq_tables_host.cu).
+struct HostTables {
+    const void *nlc_rate, *nbw_rate, *nlc_inv, *nbw_inv;
+    size_t nlc_rate_bytes, nbw_rate_bytes, nlc_inv_bytes, nbw_inv_bytes;
+};
+HostTables host_tables(int precision);
+
+}  // namespace sfq

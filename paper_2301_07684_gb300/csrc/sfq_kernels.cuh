@@ -1,0 +1,223 @@
+// sfq_kernels.cuh -- the Monte Carlo step and the batched rate / sampling kernels.
+//
+// One template serves both precisions: T = float is the mixed path (binary32
+// arithmetic, binary64 optical depth updated on the integer pipe), T = double
+// the plain binary64 path.  Equations are those of Montefiori & Tamburini,
+// "SFQEDtoolkit" (arXiv:2301.07684).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "sfq.h"
+#include "sfq_device.cuh"
+
+namespace sfq {
+
+// ---------------------------------------------------------------------------
+// Table layouts per precision (from the generated sfq_tables.inc).
+template <typename T> struct L;
+#define SFQ_LAYOUT(T, P)                                                                          \
+    template <> struct L<T> {                                                                     \
+        static constexpr int RATE_NLC_N = NLC_RATE_##P##_COUNT, RATE_NBW_N = NBW_RATE_##P##_COUNT; \
+        static constexpr int NLC_DEG = NLC_RATE_##P##_DEG, NBW_DEG = NBW_RATE_##P##_DEG;          \
+        static constexpr int NLC_ELO = NLC_RATE_##P##_X_ELO, NLC_EHI = NLC_RATE_##P##_X_EHI,      \
+                             NLC_SUB = NLC_RATE_##P##_X_SUB, NLC_LOW = NLC_RATE_##P##_X_LOW,      \
+                             NLC_SUBLOW = NLC_RATE_##P##_X_SUBLOW;                                 \
+        static constexpr int NBW_ELO = NBW_RATE_##P##_X_ELO, NBW_EHI = NBW_RATE_##P##_X_EHI,      \
+                             NBW_SUB = NBW_RATE_##P##_X_SUB, NBW_LOW = NBW_RATE_##P##_X_LOW,      \
+                             NBW_SUBLOW = NBW_RATE_##P##_X_SUBLOW;                                 \
+        static constexpr int PI_DX = NLC_INV_##P##_DX, PI_DY = NLC_INV_##P##_DY;                  \
+        static constexpr int PI_XELO = NLC_INV_##P##_X_ELO, PI_XEHI = NLC_INV_##P##_X_EHI,        \
+                             PI_XSUB = NLC_INV_##P##_X_SUB, PI_XLOW = NLC_INV_##P##_X_LOW,        \
+                             PI_XSUBLOW = NLC_INV_##P##_X_SUBLOW;                                  \
+        static constexpr int PI_YE0 = NLC_INV_##P##_Y_ELO, PI_YSUB = NLC_INV_##P##_Y_SUB,         \
+                             PI_YSUBLOW = NLC_INV_##P##_Y_SUBLOW, PI_YQLO = NLC_INV_##P##_Y_QLO,  \
+                             PI_YSUBQ = NLC_INV_##P##_Y_SUBQ, PI_NY = NLC_INV_##P##_Y_NPIECES;    \
+        static constexpr int PP_DX = NBW_INV_##P##_DX, PP_DY = NBW_INV_##P##_DY;                  \
+        static constexpr int PP_XELO = NBW_INV_##P##_X_ELO, PP_XEHI = NBW_INV_##P##_X_EHI,        \
+                             PP_XSUB = NBW_INV_##P##_X_SUB, PP_XLOW = NBW_INV_##P##_X_LOW,        \
+                             PP_XSUBLOW = NBW_INV_##P##_X_SUBLOW;                                  \
+        static constexpr int PP_YE0 = NBW_INV_##P##_Y_ELO, PP_YSUB = NBW_INV_##P##_Y_SUB,         \
+                             PP_YSUBLOW = NBW_INV_##P##_Y_SUBLOW, PP_YQLO = NBW_INV_##P##_Y_QLO,  \
+                             PP_YSUBQ = NBW_INV_##P##_Y_SUBQ, PP_NY = NBW_INV_##P##_Y_NPIECES;    \
+    };
+SFQ_LAYOUT(float, F32)
+SFQ_LAYOUT(double, F64)
+#undef SFQ_LAYOUT
+
+template <typename T>
+struct Tables {
+    const T *nlc_rate, *nbw_rate, *nlc_inv, *nbw_inv;
+};
+
+// ---------------------------------------------------------------------------
+// Fitted functions.
+// W~_rad(chi) (Eq. wtilde); `c` is the rate table (shared memory in the step kernel).
+template <typename T>
+__device__ __forceinline__ T wtilde_rad(const T *c, T chi, bool &oor) {
+    using Q = L<T>;
+    T x;
+    const int p = octave_piece<T, Q::NLC_ELO, Q::NLC_EHI, Q::NLC_SUB, Q::NLC_LOW, Q::NLC_SUBLOW>(chi, x, oor);
+    return horner1<Q::NLC_DEG>(c + p * (Q::NLC_DEG + 1), x);
+}
+
+// exp(-8/(3 chi)): binary32 with the argument carried to ~2^-48 (the argument
+// reaches 267 at chi = 0.01, where one rounding of it would cost ~1.6e-5).
+__device__ __forceinline__ float exp_m83(float chi) {
+    const float hi = 2.66666674613952636719f;                  // binary32(8/3)
+    const float lo = -7.94728632e-08f;                         // 8/3 - hi
+    const float t = hi / chi;
+    const float rem = fmaf(-t, chi, hi) + lo;                  // hi + lo - t chi (exact fma)
+    const float tl = rem / chi;
+    return expf(-t) * (1.0f - tl);
+}
+__device__ __forceinline__ double exp_m83(double chi) { return exp(-(8.0 / 3.0) / chi); }
+
+// W~_pair(chi) = chi h(chi) exp(-8/(3 chi)) (Eq. wtilde_pair); zero below 0.01 (Sec. 4.2).
+template <typename T>
+__device__ __forceinline__ T wtilde_pair(const T *c, T chi, bool &oor) {
+    using Q = L<T>;
+    if (!(chi >= (T)0.01)) return (T)0;
+    T x;
+    const int p = octave_piece<T, Q::NBW_ELO, Q::NBW_EHI, Q::NBW_SUB, Q::NBW_LOW, Q::NBW_SUBLOW>(chi, x, oor);
+    const T h = horner1<Q::NBW_DEG>(c + p * (Q::NBW_DEG + 1), x);
+    return chi * h * exp_m83(chi);
+}
+
+// s = 3 chi w^3 / 2 for w-bar = G~_pe(r, chi) (Eq. again, Eq. subs_altri).
+template <typename T>
+__device__ __forceinline__ T photon_s(const T *__restrict__ inv, T chi, T r, bool &oor) {
+    using Q = L<T>;
+    T xc, xr;
+    bool low;
+    const int ic = octave_piece<T, Q::PI_XELO, Q::PI_XEHI, Q::PI_XSUB, Q::PI_XLOW, Q::PI_XSUBLOW>(chi, xc, oor);
+    const int ir = prob_piece<T, Q::PI_YE0, Q::PI_YSUB, Q::PI_YSUBLOW, Q::PI_YQLO, Q::PI_YSUBQ>(r, xr, low, oor);
+    const T *c = inv + ((size_t)ic * Q::PI_NY + ir) * ((Q::PI_DX + 1) * (Q::PI_DY + 1));
+    T w = horner2<Q::PI_DX, Q::PI_DY>(c, xc, xr);
+    if (low) w *= r;                          // the low-r block holds w-bar / r
+    const T chi_eff = chi > (T)4096 ? (T)4096 : chi;
+    return (T)1.5 * chi_eff * w * w * w;
+}
+
+// Electron and positron shares for r (Eq. again_pp, Eq. return_to_nrg): the table
+// holds y = 1 - v-bar as a function of (chi, |r'|).
+template <typename T>
+__device__ __forceinline__ void pair_shares(const T *__restrict__ inv, T chi, T r, T &xe, T &xp, bool &oor) {
+    using Q = L<T>;
+    const T rp = (T)2 * r - (T)1;
+    const T a = fabs(rp);
+    T xc, xr;
+    bool low;
+    const int ic = octave_piece<T, Q::PP_XELO, Q::PP_XEHI, Q::PP_XSUB, Q::PP_XLOW, Q::PP_XSUBLOW>(chi, xc, oor);
+    const int ir = prob_piece<T, Q::PP_YE0, Q::PP_YSUB, Q::PP_YSUBLOW, Q::PP_YQLO, Q::PP_YSUBQ>(a, xr, low, oor);
+    const T *c = inv + ((size_t)ic * Q::PP_NY + ir) * ((Q::PP_DX + 1) * (Q::PP_DY + 1));
+    const T y = horner2<Q::PP_DX, Q::PP_DY>(c, xc, xr);
+    const T small = (T)0.5 * y, big = (T)1 - small;
+    if (rp >= (T)0) { xe = big; xp = small; }
+    else { xe = small; xp = big; }
+}
+
+// ---------------------------------------------------------------------------
+// Counters: per-thread registers, reduced per block, one atomic per counter.
+struct Cnt {
+    unsigned long long v[12];
+    __device__ void zero() {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) v[k] = 0;
+    }
+};
+enum { C_UPD, C_EV, C_EMIT, C_PAIR, C_DROP, C_SDROP, C_OOR, C_NAN, C_G1, C_RDT, C_NOEM, C_REJ };
+
+__device__ __forceinline__ void flush_counters(Cnt &c, sfq_counters *out) {
+    if (!out) return;
+    __shared__ unsigned long long red[12];
+    if (threadIdx.x < 12) red[threadIdx.x] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        unsigned long long s = c.v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+        if ((threadIdx.x & 31) == 0 && s) atomicAdd(&red[k], s);
+    }
+    __syncthreads();
+    if (threadIdx.x < 12 && red[threadIdx.x])
+        atomicAdd(reinterpret_cast<unsigned long long *>(out) + threadIdx.x, red[threadIdx.x]);
+}
+
+// ---------------------------------------------------------------------------
+// Batched rate kernels (App. A functions 5, 6).
+template <typename T, bool PAIR>
+__global__ void __launch_bounds__(256) rate_kernel(int64_t n, const T *__restrict__ gamma,
+                                                   const T *__restrict__ chi, T *__restrict__ rate,
+                                                   const T *__restrict__ table, T pref,
+                                                   sfq_counters *counters) {
+    constexpr int N = PAIR ? L<T>::RATE_NBW_N : L<T>::RATE_NLC_N;
+    __shared__ T tab[N];
+    for (int k = threadIdx.x; k < N; k += blockDim.x) tab[k] = table[k];
+    __syncthreads();
+    Cnt c;
+    c.zero();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const T g = gamma[i], x = chi[i];
+        bool oor = false;
+        T r;
+        if (!(x >= (T)0) || !(g > (T)0)) {   // NaN or invalid
+            ++c.v[C_NAN];
+            r = (T)0;
+        } else if (PAIR) {
+            r = pref * wtilde_pair<T>(tab, x, oor) / g;
+        } else {
+            r = pref * (x / g) * wtilde_rad<T>(tab, x, oor);
+        }
+        c.v[C_OOR] += oor;
+        rate[i] = r;
+    }
+    flush_counters(c, counters);
+}
+
+// Batched samplers (App. A functions 9 and 11, Eqs. again, again_pp).
+template <typename T, bool PAIR>
+__global__ void __launch_bounds__(256) sample_kernel(int64_t n, const T *__restrict__ chi,
+                                                     const T *__restrict__ r, T *__restrict__ out_a,
+                                                     T *__restrict__ out_b, const T *__restrict__ inv,
+                                                     sfq_counters *counters) {
+    Cnt c;
+    c.zero();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const T x = chi[i], u = r[i];
+        bool oor = false;
+        if (!(x >= (T)0) || !(u > (T)0) || !(u < (T)1)) {
+            ++c.v[C_NAN];
+            out_a[i] = (T)0;
+            if (out_b) out_b[i] = (T)0;
+            continue;
+        }
+        if (PAIR) {
+            T xe, xp;
+            pair_shares<T>(inv, x, u, xe, xp, oor);
+            out_a[i] = xe;
+            if (out_b) out_b[i] = xp;
+        } else {
+            const T s = photon_s<T>(inv, x, u, oor);
+            const T inv1s = (T)1 / ((T)1 + s);
+            out_a[i] = s * inv1s;          // xi = s/(1+s)
+            if (out_b) out_b[i] = inv1s;   // 1 - xi
+        }
+        c.v[C_OOR] += oor;
+    }
+    flush_counters(c, counters);
+}
+
+// Philox uniforms (4 per particle).
+template <typename T>
+__global__ void __launch_bounds__(256) uniforms_kernel(int64_t n, const uint64_t *__restrict__ id, uint32_t step,
+                                                       uint32_t tag, uint64_t seed, T *__restrict__ u) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const u4 w = draws(seed, id[i], step, tag);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) u[4 * i + k] = uniform<T>(w.w[k]);
+    }
+}
+
+}  // namespace sfq

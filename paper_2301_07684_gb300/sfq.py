@@ -1,0 +1,306 @@
+"""ctypes binding of libsfq (include/sfq.h) for PyTorch tensors.
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  Tensors must be CUDA, contiguous and of the context's precision
+(float32 for SFQ_FP32, float64 for SFQ_FP64; the optical depth is float64).
+Work is enqueued on the current torch stream.  When libsfq.so is missing the
+import of this module fails: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsfq.so")
+
+SFQ_FP32, SFQ_FP64 = 0, 1
+SFQ_ALIVE, SFQ_JUST_CREATED = 1, 2
+SFQ_SPECIES_SHIFT, SFQ_TAG_SHIFT = 2, 4
+SFQ_ELECTRON, SFQ_POSITRON, SFQ_PHOTON = 0, 1, 2
+SFQ_LEPTON_LCFA_OD, SFQ_LEPTON_BLCFA_LOCAL = 0, 1
+SFQ_FIELDS_SOA, SFQ_FIELDS_PLANE_WAVE = 0, 1
+STATUS = {0: "SFQ_OK", 1: "SFQ_ERR_ARG", 2: "SFQ_ERR_CUDA", 3: "SFQ_ERR_CAPACITY", 4: "SFQ_ERR_TABLE",
+          5: "SFQ_ERR_RANGE", 6: "SFQ_ERR_TIMEOUT"}
+COUNTER_NAMES = ["updates", "events", "emitted", "pairs", "dropped", "spawn_dropped", "out_of_range",
+                 "nan_input", "gamma_below_one", "large_rdt", "blcfa_no_emission", "blcfa_rejected"]
+
+
+class Config(C.Structure):
+    _fields_ = [("ref_len_m", C.c_double), ("ref_omega_si", C.c_double), ("dt", C.c_double),
+                ("precision", C.c_int32), ("device", C.c_int32), ("seed", C.c_uint64)]
+
+
+class Particles(C.Structure):
+    _fields_ = [("n", C.c_int64), ("px", C.c_void_p), ("py", C.c_void_p), ("pz", C.c_void_p),
+                ("tau", C.c_void_p), ("id", C.c_void_p), ("id_base", C.c_uint64), ("flags", C.c_void_p),
+                ("fprev", C.c_void_p * 3), ("dfprev", C.c_void_p * 3), ("lepton_model", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class Fields(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("ex", C.c_void_p), ("ey", C.c_void_p),
+                ("ez", C.c_void_p), ("bx", C.c_void_p), ("by", C.c_void_p), ("bz", C.c_void_p),
+                ("k0", C.c_void_p), ("amp", C.c_void_p), ("amp0", C.c_double), ("table", C.c_void_p),
+                ("n_table", C.c_uint32), ("k_step", C.c_uint32)]
+
+
+class Products(C.Structure):
+    _fields_ = [("capacity", C.c_int64), ("px", C.c_void_p), ("py", C.c_void_p), ("pz", C.c_void_p),
+                ("parent_id", C.c_void_p), ("step", C.c_void_p), ("meta", C.c_void_p), ("count", C.c_void_p)]
+
+
+class Spawn(C.Structure):
+    _fields_ = [("p", Particles), ("k0", C.c_void_p), ("amp", C.c_void_p), ("count", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2301_07684_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i64, u32, st = C.c_void_p, C.c_int64, C.c_uint32, C.c_int
+        L.sfq_init.argtypes = [C.POINTER(Config), C.POINTER(vp)]
+        L.sfq_init.restype = st
+        L.sfq_finalize.argtypes = [vp]
+        L.sfq_finalize.restype = None
+        L.sfq_last_error.argtypes = [vp]
+        L.sfq_last_error.restype = C.c_char_p
+        L.sfq_constants.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.sfq_constants.restype = st
+        for name in ("sfq_photon_rate", "sfq_pair_rate"):
+            getattr(L, name).argtypes = [vp, i64, vp, vp, vp, vp, vp]
+            getattr(L, name).restype = st
+        L.sfq_uniforms.argtypes = [vp, i64, vp, u32, u32, vp, vp]
+        L.sfq_uniforms.restype = st
+        for name in ("sfq_sample_photon_xi", "sfq_sample_pair_xi"):
+            getattr(L, name).argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
+            getattr(L, name).restype = st
+        L.sfq_mc_step.argtypes = [vp, C.POINTER(Particles), C.POINTER(Fields), u32, C.POINTER(Products),
+                                  C.POINTER(Spawn), vp, vp]
+        L.sfq_mc_step.restype = st
+        L.sfq_version.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+EXPORTED = ["sfq_init", "sfq_finalize", "sfq_last_error", "sfq_constants", "sfq_photon_rate", "sfq_pair_rate",
+            "sfq_uniforms", "sfq_sample_photon_xi", "sfq_sample_pair_xi", "sfq_mc_step", "sfq_version"]
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class SfqError(RuntimeError):
+    pass
+
+
+def counters_tensor(device="cuda"):
+    """Zeroed sfq_counters on the device (16 uint64 words)."""
+    return torch.zeros(16, dtype=torch.int64, device=device)
+
+
+def counters_dict(t):
+    v = t.cpu().tolist()
+    return {k: int(v[i]) for i, k in enumerate(COUNTER_NAMES)}
+
+
+class Context:
+    """One libsfq context (sfq_init / sfq_finalize)."""
+
+    def __init__(self, *, ref_len_m=0.0, ref_omega_si=0.0, dt, precision="fp32", device=None, seed=0):
+        self.precision = SFQ_FP64 if precision in ("fp64", SFQ_FP64) else SFQ_FP32
+        self.dtype = torch.float64 if self.precision == SFQ_FP64 else torch.float32
+        dev = torch.cuda.current_device() if device is None else int(device)
+        self.device = torch.device("cuda", dev)
+        cfg = Config(ref_len_m=ref_len_m, ref_omega_si=ref_omega_si, dt=dt, precision=self.precision,
+                     device=dev, seed=seed)
+        h = C.c_void_p()
+        st = lib().sfq_init(C.byref(cfg), C.byref(h))
+        if st != 0:
+            raise SfqError(f"sfq_init: {STATUS.get(st, st)}")
+        self._h = h
+        self.dt = dt
+        self.seed = seed
+        rho, pref = C.c_double(), C.c_double()
+        lib().sfq_constants(h, C.byref(rho), C.byref(pref))
+        self.rho, self.pref = rho.value, pref.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sfq_finalize(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != 0:
+            msg = lib().sfq_last_error(self._h).decode()
+            raise SfqError(f"{what}: {STATUS.get(st, st)}: {msg}")
+
+    def _real(self, t, name):
+        if t.dtype != self.dtype or not t.is_cuda or not t.is_contiguous():
+            raise SfqError(f"{name}: expected a contiguous CUDA {self.dtype} tensor")
+        return t
+
+    # --- entry points -------------------------------------------------------
+    def photon_rate(self, gamma, chi, out=None, counters=None):
+        out = torch.empty_like(chi) if out is None else out
+        self._check(lib().sfq_photon_rate(self._h, chi.numel(), _ptr(self._real(gamma, "gamma")),
+                                          _ptr(self._real(chi, "chi")), _ptr(self._real(out, "rate")),
+                                          _ptr(counters), _stream()), "sfq_photon_rate")
+        return out
+
+    def pair_rate(self, gamma, chi, out=None, counters=None):
+        out = torch.empty_like(chi) if out is None else out
+        self._check(lib().sfq_pair_rate(self._h, chi.numel(), _ptr(self._real(gamma, "gamma")),
+                                        _ptr(self._real(chi, "chi")), _ptr(self._real(out, "rate")),
+                                        _ptr(counters), _stream()), "sfq_pair_rate")
+        return out
+
+    def uniforms(self, ids, step, tag=0):
+        u = torch.empty(ids.numel(), 4, dtype=self.dtype, device=ids.device)
+        self._check(lib().sfq_uniforms(self._h, ids.numel(), _ptr(ids), step, tag, _ptr(u), _stream()),
+                    "sfq_uniforms")
+        return u
+
+    def sample_photon_xi(self, chi, r, counters=None):
+        xi = torch.empty_like(chi)
+        xic = torch.empty_like(chi)
+        self._check(lib().sfq_sample_photon_xi(self._h, chi.numel(), _ptr(self._real(chi, "chi")),
+                                               _ptr(self._real(r, "r")), _ptr(xi), _ptr(xic), _ptr(counters),
+                                               _stream()), "sfq_sample_photon_xi")
+        return xi, xic
+
+    def sample_pair_xi(self, chi, r, counters=None):
+        xe = torch.empty_like(chi)
+        xp = torch.empty_like(chi)
+        self._check(lib().sfq_sample_pair_xi(self._h, chi.numel(), _ptr(self._real(chi, "chi")),
+                                             _ptr(self._real(r, "r")), _ptr(xe), _ptr(xp), _ptr(counters),
+                                             _stream()), "sfq_sample_pair_xi")
+        return xe, xp
+
+    def mc_step(self, particles: "ParticleBuffers", fields: "FieldSource", step: int, products: "ProductBuffers",
+                spawn: "SpawnBuffers" = None, counters=None):
+        P = particles.descriptor()
+        F = fields.descriptor()
+        O = products.descriptor()
+        S = spawn.descriptor() if spawn is not None else None
+        self._check(lib().sfq_mc_step(self._h, C.byref(P), C.byref(F), step, C.byref(O),
+                                      C.byref(S) if S is not None else None, _ptr(counters), _stream()),
+                    "sfq_mc_step")
+
+
+# --- buffers -------------------------------------------------------------------
+class ParticleBuffers:
+    """Structure-of-arrays particle state on the device."""
+
+    def __init__(self, px, py, pz, tau, flags, ids=None, id_base=0, fprev=None, dfprev=None,
+                 lepton_model=SFQ_LEPTON_LCFA_OD):
+        self.px, self.py, self.pz, self.tau, self.flags = px, py, pz, tau, flags
+        self.ids, self.id_base = ids, id_base
+        self.fprev, self.dfprev = fprev, dfprev
+        self.lepton_model = lepton_model
+        self.n = px.numel()
+
+    def descriptor(self, n=None):
+        P = Particles()
+        P.n = self.n if n is None else n
+        P.px, P.py, P.pz = _ptr(self.px), _ptr(self.py), _ptr(self.pz)
+        P.tau, P.flags = _ptr(self.tau), _ptr(self.flags)
+        P.id = _ptr(self.ids)
+        P.id_base = self.id_base
+        for k in range(3):
+            P.fprev[k] = _ptr(self.fprev[k]) if self.fprev is not None else None
+            P.dfprev[k] = _ptr(self.dfprev[k]) if self.dfprev is not None else None
+        P.lepton_model = self.lepton_model
+        return P
+
+
+class FieldSource:
+    def __init__(self, kind, ex=None, ey=None, ez=None, bx=None, by=None, bz=None, k0=None, amp=None, amp0=0.0,
+                 table=None, k_step=0):
+        self.kind = kind
+        self.ex, self.ey, self.ez, self.bx, self.by, self.bz = ex, ey, ez, bx, by, bz
+        self.k0, self.amp, self.amp0, self.table, self.k_step = k0, amp, amp0, table, k_step
+
+    @staticmethod
+    def soa(ex, ey, ez, bx, by, bz):
+        return FieldSource(SFQ_FIELDS_SOA, ex, ey, ez, bx, by, bz)
+
+    @staticmethod
+    def plane_wave(k0, table, k_step, amp=None, amp0=0.0):
+        return FieldSource(SFQ_FIELDS_PLANE_WAVE, k0=k0, table=table, k_step=k_step, amp=amp, amp0=amp0)
+
+    def descriptor(self):
+        F = Fields()
+        F.kind = self.kind
+        F.ex, F.ey, F.ez = _ptr(self.ex), _ptr(self.ey), _ptr(self.ez)
+        F.bx, F.by, F.bz = _ptr(self.bx), _ptr(self.by), _ptr(self.bz)
+        F.k0, F.amp, F.amp0 = _ptr(self.k0), _ptr(self.amp), float(self.amp0)
+        F.table = _ptr(self.table)
+        F.n_table = 0 if self.table is None else self.table.numel()
+        F.k_step = self.k_step
+        return F
+
+
+class ProductBuffers:
+    def __init__(self, capacity, dtype, device):
+        self.capacity = capacity
+        pad = max(capacity, 1)
+        self.px = torch.empty(pad, dtype=dtype, device=device)
+        self.py = torch.empty(pad, dtype=dtype, device=device)
+        self.pz = torch.empty(pad, dtype=dtype, device=device)
+        self.parent_id = torch.empty(pad, dtype=torch.int64, device=device)
+        self.step = torch.empty(pad, dtype=torch.int32, device=device)
+        self.meta = torch.empty(pad, dtype=torch.uint8, device=device)
+        self.count = torch.zeros(2, dtype=torch.int64, device=device)
+
+    def reset(self):
+        self.count.zero_()
+
+    def n(self):
+        return int(self.count[0].item())
+
+    def descriptor(self):
+        O = Products()
+        O.capacity = self.capacity
+        O.px, O.py, O.pz = _ptr(self.px), _ptr(self.py), _ptr(self.pz)
+        O.parent_id, O.step, O.meta = _ptr(self.parent_id), _ptr(self.step), _ptr(self.meta)
+        O.count = _ptr(self.count)
+        return O
+
+    def to_numpy(self):
+        k = min(self.n(), self.capacity)
+        return dict(px=self.px[:k].cpu().numpy(), py=self.py[:k].cpu().numpy(), pz=self.pz[:k].cpu().numpy(),
+                    parent_id=self.parent_id[:k].cpu().numpy().view("uint64"),
+                    step=self.step[:k].cpu().numpy().view("uint32"), meta=self.meta[:k].cpu().numpy())
+
+
+class SpawnBuffers:
+    def __init__(self, particles: ParticleBuffers, k0=None, amp=None):
+        self.particles, self.k0, self.amp = particles, k0, amp
+        self.count = torch.zeros(2, dtype=torch.int64, device=particles.px.device)
+
+    def descriptor(self):
+        S = Spawn()
+        S.p = self.particles.descriptor()
+        S.k0, S.amp = _ptr(self.k0), _ptr(self.amp)
+        S.count = _ptr(self.count)
+        return S
