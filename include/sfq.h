@@ -198,7 +198,8 @@ typedef struct sfq_counters {
     unsigned long long large_rdt;        /* R dt > 0.1 (Sec. 2: R dt << 1 is assumed) */
     unsigned long long blcfa_no_emission;/* threshold >= 0.75 gamma (Sec. 5) */
     unsigned long long blcfa_rejected;   /* rejected by Eq. rej_cond */
-    unsigned long long reserved[4];
+    unsigned long long timeouts;         /* bounded device waits that gave up (0 in a correct run) */
+    unsigned long long reserved[3];
 } sfq_counters;
 
 /* One Monte Carlo step for every alive particle of `p` (Sec. 2 and 4; Sec. 5 for
@@ -213,6 +214,16 @@ typedef struct sfq_counters {
 sfq_status sfq_mc_step(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, uint32_t step,
                        const sfq_products *out, const sfq_spawn *spawn, sfq_counters *counters,
                        void *stream);
+
+/* Launch shape of sfq_mc_step for this context, the knob the autotuner turns.
+ *   variant: 0 = automatic; 1 = warp-streaming kernel (each warp loads its particles
+ *            directly); 2 = TMA-staged kernel (bulk copies of each tile into shared
+ *            memory, one persistent block per SM).
+ *   ppt:     particles per lane per chunk of the warp-streaming kernel (1, 2 or 4;
+ *            0 = default).
+ *   grid_blocks: grid size (0 = one wave of resident blocks on every SM).
+ * Returns SFQ_ERR_ARG for other values.  Results do not depend on the shape. */
+sfq_status sfq_set_step_shape(sfq_ctx *ctx, int32_t variant, int32_t ppt, int32_t grid_blocks);
 
 /* Library version string. */
 const char *sfq_version(void);

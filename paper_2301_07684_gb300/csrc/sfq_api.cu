@@ -225,11 +225,22 @@ sfq_status sfq_mc_step(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f
     }
     if (counters && !aligned8(counters)) return fail(ctx, SFQ_ERR_ARG, "counters misaligned");
     DeviceGuard g(ctx->device);
-    const int ppt = is_fp64(ctx) ? 1 : 2;
-    sfq::StepLaunch L{ctx, p, f, step, out, spawn, counters, (cudaStream_t)stream,
-                      grid_for(ctx, p->n, 256 * ppt), ppt};
+    const int ppt = ctx->step_ppt ? ctx->step_ppt : (is_fp64(ctx) ? 1 : 2);
+    sfq::StepLaunch L{ctx, p, f, step, out, spawn, counters, (cudaStream_t)stream, ctx->step_grid, ppt,
+                      ctx->step_variant};
     const cudaError_t e = is_fp64(ctx) ? sfq::launch_step_f64(L) : sfq::launch_step_f32(L);
     return e == cudaSuccess ? SFQ_OK : cuda_fail(ctx, e, "sfq_mc_step");
+}
+
+sfq_status sfq_set_step_shape(sfq_ctx *ctx, int32_t variant, int32_t ppt, int32_t grid_blocks) {
+    if (!ctx) return SFQ_ERR_ARG;
+    if (variant < 0 || variant > 2) return fail(ctx, SFQ_ERR_ARG, "variant must be 0, 1 or 2");
+    if (!(ppt == 0 || ppt == 1 || ppt == 2 || ppt == 4)) return fail(ctx, SFQ_ERR_ARG, "ppt must be 0, 1, 2 or 4");
+    if (grid_blocks < 0) return fail(ctx, SFQ_ERR_ARG, "grid_blocks < 0");
+    ctx->step_variant = variant;
+    ctx->step_ppt = ppt;
+    ctx->step_grid = grid_blocks;
+    return SFQ_OK;
 }
 
 }  // extern "C"

@@ -81,6 +81,21 @@ __host__ __device__ constexpr T pow2(int k) {
 //                + octaves of q = 1 - r, e = -2 down to QLO, 2^SUBQ each (q = 1/2 closes the first).
 // Each returns the piece index and the local variable x in [-1, 1]; all steps are
 // exact (scaling by powers of two and Sterbenz subtractions).
+// Sub-piece j (top SUB mantissa bits) and local variable x in [-1, 1) of a value with
+// mantissa m in [1, 2): x = 2 (frac(2^SUB (m - 1))) - 1, formed from the bits.
+template <typename T, int SUB>
+__device__ __forceinline__ int mant_split(T v, T &x) {
+    using U = typename fp<T>::U;
+    constexpr int M = fp<T>::MANT;
+    const U b = fp<T>::bits(v);
+    const U frac = b & ((((U)1) << M) - 1);
+    const int j = SUB ? (int)(frac >> (M - SUB)) : 0;
+    const U rest = SUB ? ((frac << SUB) & ((((U)1) << M) - 1)) : frac;
+    const T one_plus = fp<T>::from(fp<T>::bits((T)1) | rest);          // 1 + fractional part
+    x = (T)2 * one_plus - (T)3;
+    return j;
+}
+
 template <typename T, int ELO, int EHI, int SUB, int LOW, int SUBLOW>
 __device__ __forceinline__ int octave_piece(T v, T &x, bool &oor) {
     constexpr int NLOW = LOW ? (1 << SUBLOW) : 0;
@@ -89,7 +104,7 @@ __device__ __forceinline__ int octave_piece(T v, T &x, bool &oor) {
     if (e < ELO) {                     // zero, subnormal or below the first octave
         if (LOW) {
             const T t = v * pow2<T>(SUBLOW - ELO);
-            int j = (int)t;
+            int j = SUBLOW ? (int)t : 0;
             j = j > NLOW - 1 ? NLOW - 1 : j;
             x = (T)2 * (t - (T)j) - (T)1;
             return j;
@@ -103,9 +118,7 @@ __device__ __forceinline__ int octave_piece(T v, T &x, bool &oor) {
         x = (T)1;
         return NPIECES - 1;
     }
-    const T t = (fp<T>::mant(v) - (T)1) * (T)(1 << SUB);
-    const int j = (int)t;
-    x = (T)2 * (t - (T)j) - (T)1;
+    const int j = mant_split<T, SUB>(v, x);
     return NLOW + (e - ELO) * (1 << SUB) + j;
 }
 
@@ -118,15 +131,13 @@ __device__ __forceinline__ int prob_piece(T r, T &x, bool &low, bool &oor) {
         const int e = fp<T>::expo(r);
         if (e < E0) {
             const T t = r * pow2<T>(SUBLOW - E0);
-            int j = (int)t;
+            int j = SUBLOW ? (int)t : 0;
             j = j > NLOW - 1 ? NLOW - 1 : j;
             x = (T)2 * (t - (T)j) - (T)1;
             low = true;
             return j;
         }
-        const T t = (fp<T>::mant(r) - (T)1) * (T)(1 << SUB);
-        const int j = (int)t;
-        x = (T)2 * (t - (T)j) - (T)1;
+        const int j = mant_split<T, SUB>(r, x);
         return NLOW + (e - E0) * (1 << SUB) + j;
     }
     const T q = (T)1 - r;              // exact for r >= 1/2
@@ -142,9 +153,7 @@ __device__ __forceinline__ int prob_piece(T r, T &x, bool &low, bool &oor) {
         j = 0;
         x = (T)-1;
     } else {
-        const T t = (fp<T>::mant(q) - (T)1) * (T)(1 << SUBQ);
-        j = (int)t;
-        x = (T)2 * (t - (T)j) - (T)1;
+        j = mant_split<T, SUBQ>(q, x);
     }
     return NLOW + NROCT + (-2 - e) * (1 << SUBQ) + j;
 }
@@ -173,6 +182,22 @@ __device__ __forceinline__ T horner2(const T *__restrict__ c, T x, T y) {
     }
     return acc;
 }
+
+// ---------------------------------------------------------------------------
+// Square root and reciprocal square root from the hardware estimate plus one Newton
+// step (about 1 ulp in binary32; the binary64 versions use the library functions).
+__device__ __forceinline__ float sqrt_nr(float q) {
+    if (!(q > 0.0f)) return 0.0f;
+    const float r = rsqrtf(q);
+    const float s = q * r;
+    return fmaf(0.5f * r, fmaf(-s, s, q), s);
+}
+__device__ __forceinline__ double sqrt_nr(double q) { return q > 0.0 ? sqrt(q) : 0.0; }
+__device__ __forceinline__ float rsqrt_nr(float q) {
+    const float r = rsqrtf(q);
+    return fmaf(0.5f * r, fmaf(-q * r, r, 1.0f), r);
+}
+__device__ __forceinline__ double rsqrt_nr(double q) { return rsqrt(q); }
 
 // ---------------------------------------------------------------------------
 // Optical depth in binary64 updated on the integer pipe (GB300's FP64 pipe runs at

@@ -14,6 +14,9 @@ struct sfq_ctx {
     // device copies of the fitted tables (one precision per context)
     void *d_nlc_rate, *d_nbw_rate, *d_nlc_inv, *d_nbw_inv;
     int num_sms;
+    int step_variant = 0;    // 0 = automatic, 1 = warp-streaming, 2 = TMA-staged
+    int step_ppt = 0;        // 0 = default
+    int step_grid = 0;       // 0 = one wave of resident blocks
     std::string err;
 };
 
@@ -50,6 +53,7 @@ struct StepLaunch {
     cudaStream_t stream;
     int grid;
     int ppt;
+    int variant;
 };
 
 cudaError_t launch_rate_f32(const RateLaunch &, bool pair);

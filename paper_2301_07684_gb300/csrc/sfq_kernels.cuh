@@ -50,15 +50,66 @@ struct Tables {
     const T *nlc_rate, *nbw_rate, *nlc_inv, *nbw_inv;
 };
 
+// Rate tables in shared memory: each piece padded to a multiple of 16 bytes so that
+// its coefficients are read with vector loads.
+template <typename T, int DEG>
+struct Padded {
+    static constexpr int V = 16 / (int)sizeof(T);
+    static constexpr int STRIDE = ((DEG + 1) + V - 1) / V * V;
+};
+template <typename T>
+struct RateSmem {
+    using Q = L<T>;
+    static constexpr int NLC_STRIDE = Padded<T, Q::NLC_DEG>::STRIDE;
+    static constexpr int NBW_STRIDE = Padded<T, Q::NBW_DEG>::STRIDE;
+    static constexpr int NLC_N = Q::RATE_NLC_N / (Q::NLC_DEG + 1) * NLC_STRIDE;
+    static constexpr int NBW_N = Q::RATE_NBW_N / (Q::NBW_DEG + 1) * NBW_STRIDE;
+};
+// Copy a rate table into padded shared memory (all threads of the block take part).
+template <typename T, int DEG, int STRIDE>
+__device__ __forceinline__ void stage_rate_table(T *dst, const T *src, int npieces, int tid, int nthreads) {
+    for (int k = tid; k < npieces * STRIDE; k += nthreads) {
+        const int p = k / STRIDE, c = k - p * STRIDE;
+        dst[k] = c <= DEG ? src[p * (DEG + 1) + c] : (T)0;
+    }
+}
+template <int DEG, int STRIDE>
+__device__ __forceinline__ float horner_smem(const float *c, float x) {
+    float co[STRIDE];
+#pragma unroll
+    for (int k = 0; k < STRIDE / 4; ++k) {
+        const float4 v = reinterpret_cast<const float4 *>(c)[k];
+        co[4 * k] = v.x; co[4 * k + 1] = v.y; co[4 * k + 2] = v.z; co[4 * k + 3] = v.w;
+    }
+    float acc = co[DEG];
+#pragma unroll
+    for (int k = DEG - 1; k >= 0; --k) acc = fmaf(acc, x, co[k]);
+    return acc;
+}
+template <int DEG, int STRIDE>
+__device__ __forceinline__ double horner_smem(const double *c, double x) {
+    double co[STRIDE];
+#pragma unroll
+    for (int k = 0; k < STRIDE / 2; ++k) {
+        const double2 v = reinterpret_cast<const double2 *>(c)[k];
+        co[2 * k] = v.x; co[2 * k + 1] = v.y;
+    }
+    double acc = co[DEG];
+#pragma unroll
+    for (int k = DEG - 1; k >= 0; --k) acc = fma(acc, x, co[k]);
+    return acc;
+}
+
 // ---------------------------------------------------------------------------
 // Fitted functions.
 // W~_rad(chi) (Eq. wtilde); `c` is the rate table (shared memory in the step kernel).
 template <typename T>
 __device__ __forceinline__ T wtilde_rad(const T *c, T chi, bool &oor) {
     using Q = L<T>;
+    constexpr int ST = RateSmem<T>::NLC_STRIDE;
     T x;
     const int p = octave_piece<T, Q::NLC_ELO, Q::NLC_EHI, Q::NLC_SUB, Q::NLC_LOW, Q::NLC_SUBLOW>(chi, x, oor);
-    return horner1<Q::NLC_DEG>(c + p * (Q::NLC_DEG + 1), x);
+    return horner_smem<Q::NLC_DEG, ST>(c + p * ST, x);
 }
 
 // exp(-8/(3 chi)): binary32 with the argument carried to ~2^-48 (the argument
@@ -79,8 +130,9 @@ __device__ __forceinline__ T wtilde_pair(const T *c, T chi, bool &oor) {
     using Q = L<T>;
     if (!(chi >= (T)0.01)) return (T)0;
     T x;
+    constexpr int ST = RateSmem<T>::NBW_STRIDE;
     const int p = octave_piece<T, Q::NBW_ELO, Q::NBW_EHI, Q::NBW_SUB, Q::NBW_LOW, Q::NBW_SUBLOW>(chi, x, oor);
-    const T h = horner1<Q::NBW_DEG>(c + p * (Q::NBW_DEG + 1), x);
+    const T h = horner_smem<Q::NBW_DEG, ST>(c + p * ST, x);
     return chi * h * exp_m83(chi);
 }
 
@@ -120,7 +172,7 @@ __device__ __forceinline__ void pair_shares(const T *__restrict__ inv, T chi, T 
 // ---------------------------------------------------------------------------
 // Counters: per-thread registers, reduced per block, one atomic per counter.
 struct Cnt {
-    unsigned long long v[12];
+    uint32_t v[12];     // per-thread counts of one launch (fit in 32 bits); widened when flushed
     __device__ void zero() {
 #pragma unroll
         for (int k = 0; k < 12; ++k) v[k] = 0;
@@ -135,7 +187,7 @@ __device__ __forceinline__ void flush_counters(Cnt &c, sfq_counters *out) {
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-        unsigned long long s = c.v[k];
+        unsigned long long s = (unsigned long long)c.v[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
         if ((threadIdx.x & 31) == 0 && s) atomicAdd(&red[k], s);
@@ -152,9 +204,15 @@ __global__ void __launch_bounds__(256) rate_kernel(int64_t n, const T *__restric
                                                    const T *__restrict__ chi, T *__restrict__ rate,
                                                    const T *__restrict__ table, T pref,
                                                    sfq_counters *counters) {
-    constexpr int N = PAIR ? L<T>::RATE_NBW_N : L<T>::RATE_NLC_N;
-    __shared__ T tab[N];
-    for (int k = threadIdx.x; k < N; k += blockDim.x) tab[k] = table[k];
+    using RS = RateSmem<T>;
+    constexpr int N = PAIR ? RS::NBW_N : RS::NLC_N;
+    __shared__ __align__(16) T tab[N];
+    if (PAIR)
+        stage_rate_table<T, L<T>::NBW_DEG, RS::NBW_STRIDE>(tab, table, L<T>::RATE_NBW_N / (L<T>::NBW_DEG + 1),
+                                                            threadIdx.x, blockDim.x);
+    else
+        stage_rate_table<T, L<T>::NLC_DEG, RS::NLC_STRIDE>(tab, table, L<T>::RATE_NLC_N / (L<T>::NLC_DEG + 1),
+                                                            threadIdx.x, blockDim.x);
     __syncthreads();
     Cnt c;
     c.zero();

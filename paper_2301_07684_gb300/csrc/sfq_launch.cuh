@@ -2,7 +2,7 @@
 // sfq_launch_f64.cu with SFQ_T set to float or double.
 #pragma once
 #include "sfq_internal.h"
-#include "sfq_step.cuh"
+#include "sfq_step_tma.cuh"
 
 namespace sfq {
 
@@ -101,15 +101,47 @@ static cudaError_t launch_step_t(const StepLaunch &L) {
     a.tab = tables_of<T>(ctx);
     a.counters = L.counters;
     const bool pw = f.kind == SFQ_FIELDS_PLANE_WAVE;
-    // particles per thread per tile: 2 (default) or 1 / 4 as chosen by the caller's autotuner
-    switch ((pw ? 10 : 0) + L.ppt) {
-        case 1: mc_step_kernel<T, FK_SOA, 1><<<L.grid, STEP_BS, 0, L.stream>>>(a); break;
-        case 4: mc_step_kernel<T, FK_SOA, 4><<<L.grid, STEP_BS, 0, L.stream>>>(a); break;
-        case 11: mc_step_kernel<T, FK_PW, 1><<<L.grid, STEP_BS, 0, L.stream>>>(a); break;
-        case 14: mc_step_kernel<T, FK_PW, 4><<<L.grid, STEP_BS, 0, L.stream>>>(a); break;
-        case 12: mc_step_kernel<T, FK_PW, 2><<<L.grid, STEP_BS, 0, L.stream>>>(a); break;
-        default: mc_step_kernel<T, FK_SOA, 2><<<L.grid, STEP_BS, 0, L.stream>>>(a); break;
+    // TMA-staged kernel: one persistent block per SM; chosen automatically when every
+    // SM gets at least one full tile
+    constexpr int TILE = TmaStage<T, FK_SOA>::TILE;
+    const bool tma = L.variant == 2 || (L.variant == 0 && p.n >= (int64_t)TILE * ctx->num_sms);
+    if (tma) {
+        // 16 consumer warps with 1024/16 particles each, or 8 warps with twice as many per lane (ppt = 4)
+        const bool w8 = L.ppt == 4;
+        void (*kern)(const StepArgs<T>) =
+            pw ? (w8 ? mc_step_tma_kernel<T, FK_PW, 8> : mc_step_tma_kernel<T, FK_PW, 16>)
+               : (w8 ? mc_step_tma_kernel<T, FK_SOA, 8> : mc_step_tma_kernel<T, FK_SOA, 16>);
+        const int threads = 32 * ((w8 ? 8 : 16) + 1);
+        const size_t smem = pw ? tma_smem_bytes<T, FK_PW>() : tma_smem_bytes<T, FK_SOA>();
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const int64_t ntiles = (p.n + TILE - 1) / TILE;
+        int grid = L.grid > 0 ? L.grid : ctx->num_sms;
+        if (ntiles < grid) grid = (int)ntiles;
+        kern<<<grid, threads, smem, L.stream>>>(a);
+        return cudaGetLastError();
     }
+    void (*kern)(const StepArgs<T>) = nullptr;
+    switch ((pw ? 10 : 0) + L.ppt) {
+        case 1: kern = mc_step_kernel<T, FK_SOA, 1>; break;
+        case 4: kern = mc_step_kernel<T, FK_SOA, 4>; break;
+        case 11: kern = mc_step_kernel<T, FK_PW, 1>; break;
+        case 12: kern = mc_step_kernel<T, FK_PW, 2>; break;
+        case 14: kern = mc_step_kernel<T, FK_PW, 4>; break;
+        default: kern = mc_step_kernel<T, FK_SOA, 2>; break;
+    }
+    int grid = L.grid;
+    if (grid <= 0) {
+        // one wave of resident blocks: a multiple of the SM count
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, STEP_BS, 0);
+        if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+        grid = per_sm * ctx->num_sms;
+        const int64_t chunks = (p.n + 32 * L.ppt - 1) / (32 * L.ppt);
+        const int64_t need = (chunks + STEP_BS / 32 - 1) / (STEP_BS / 32);
+        if (need < grid) grid = (int)(need > 0 ? need : 1);
+    }
+    kern<<<grid, STEP_BS, 0, L.stream>>>(a);
     return cudaGetLastError();
 }
 

@@ -58,14 +58,15 @@ struct StepArgs {
 
 template <typename T>
 struct QEntry {
-    int lidx;           // index within the tile
-    uint16_t o_prod, o_spawn;
+    int64_t i;          // particle index
     T g;                // energy of the particle
-    T a;                // chi in phase A; then s (emission) or xi_e (pair)
-    T b;                // xi_p (pair)
+    T chi;              // quantum parameter at the event
 };
 
 constexpr int STEP_BS = 256;
+#ifndef SFQ_STEP_MINB
+#define SFQ_STEP_MINB 4   // resident blocks per SM the register allocation aims for (measured best)
+#endif
 
 enum { FK_SOA = 0, FK_PW = 1 };
 
@@ -93,36 +94,35 @@ __device__ __forceinline__ T chi_of(T g, T px, T py, T pz, const T E[3], const T
     const T fz = fma(g, E[2], px * B[1] - py * B[0]);
     const T pe = fma(px, E[0], fma(py, E[1], pz * E[2]));
     const T q = fma(fx, fx, fma(fy, fy, fz * fz)) - pe * pe;
-    return sqrt(q > (T)0 ? q : (T)0) * inv_rho;
+    return sqrt_nr(q) * inv_rho;
 }
 
 // Optical-depth decrement (Sec. 2).  Returns true on an event; otherwise stores
 // the new tau.  `draw0` holds -ln(u3) when the particle arrived without one.
-__device__ __forceinline__ bool od_update(double *tau_ptr, float d, uint64_t seed, uint64_t id,
+template <typename IdF>
+__device__ __forceinline__ bool od_update(double *tau_ptr, float d, uint64_t seed, IdF id_of,
                                           uint32_t step, uint32_t tag) {
     uint64_t b = (uint64_t)__double_as_longlong(*tau_ptr);
-    uint64_t q;
     if (b >> 63) {                                  // no optical depth yet: draw it (word 3)
-        const u4 w = draws(seed, id, step, tag);
+        const u4 w = draws(seed, id_of(), step, tag);
         const float t0 = -logf(uniform<float>(w.w[3]));
         b = f32_to_f64_bits(t0);
     }
-    if (!tau_to_fixed(b, q)) {                      // tau >= 32: plain binary64
-        const double t = __longlong_as_double((long long)b) - (double)d;
-        if (t < 0.0) return true;
-        *tau_ptr = t;
-        return false;
-    }
-    const uint64_t D = dec_to_fixed(d);
-    if (D > q) return true;
-    *tau_ptr = __longlong_as_double((long long)fixed_to_tau(q - D));
+    // tau_d - R dt in binary64: the binary32 decrement is widened exactly with integer
+    // operations and the subtraction is the only binary64 instruction of the update
+    const uint32_t db = __float_as_uint(d);
+    const uint64_t dd = ((db >> 23) - 1u < 254u) ? f32_to_f64_bits(d) : 0ull;   // normal d > 0, else 0
+    const double t = __dsub_rn(__longlong_as_double((long long)b), __longlong_as_double((long long)dd));
+    if (t < 0.0) return true;
+    *tau_ptr = t;
     return false;
 }
-__device__ __forceinline__ bool od_update(double *tau_ptr, double d, uint64_t seed, uint64_t id,
+template <typename IdF>
+__device__ __forceinline__ bool od_update(double *tau_ptr, double d, uint64_t seed, IdF id_of,
                                           uint32_t step, uint32_t tag) {
     double t = *tau_ptr;
     if (t < 0.0 || signbit(t)) {
-        const u4 w = draws(seed, id, step, tag);
+        const u4 w = draws(seed, id_of(), step, tag);
         t = -log(uniform<double>(w.w[3]));
     }
     t = t - d;
@@ -148,173 +148,206 @@ __device__ __forceinline__ T lepton_pmag(T g, Cnt &c) {
     return sqrt(q);
 }
 
-// T: float (mixed) or double; FK: field source; PPT: particles per thread per tile.
+// One batch of up to 32 queued events, one per lane (lanes >= nvalid idle); all
+// 32 lanes execute it (warp shuffles).  Sampling (Eq. again / Eq. again_pp),
+// parent update and product records; one global atomic per batch reserves the
+// records.
+template <typename T>
+__device__ __forceinline__ void process_events(const StepArgs<T> &a, const QEntry<T> &e, bool valid, Cnt &c) {
+    const int lane = threadIdx.x & 31;
+    int nprod = 0, nspawn = 0;
+    T px = 0, py = 0, pz = 0, xa = 0, xb = 0;
+    uint8_t fl = 0;
+    uint64_t id = 0;
+    uint32_t tag = 0;
+    bool photon = false;
+    bool oor = false;
+    if (valid) {
+        fl = a.flags[e.i];
+        id = a.id ? a.id[e.i] : a.id_base + (uint64_t)e.i;
+        tag = (fl >> SFQ_TAG_SHIFT) & 3u;
+        px = a.px[e.i]; py = a.py[e.i]; pz = a.pz[e.i];
+        photon = ((fl >> SFQ_SPECIES_SHIFT) & 3) == SFQ_PHOTON;
+        const u4 w = draws(a.seed, id, a.step, tag);
+        const T r1 = uniform<T>(w.w[1]);
+        ++c.v[C_EV];
+        if (photon) {
+            pair_shares<T>(a.tab.nbw_inv, e.chi, r1, xa, xb, oor);
+            nprod = 2;
+            nspawn = a.scount ? 2 : 0;
+            ++c.v[C_PAIR];
+        } else {
+            xa = photon_s<T>(a.tab.nlc_inv, e.chi, r1, oor);      // s
+            xb = uniform<T>(w.w[0]);                               // for the fresh optical depth
+            nprod = 1;
+            ++c.v[C_EMIT];
+        }
+        c.v[C_OOR] += oor;
+    }
+    // warp prefix sums of the record counts
+    int pre_p = nprod, pre_s = nspawn;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int tp = __shfl_up_sync(0xFFFFFFFFu, pre_p, o);
+        const int ts = __shfl_up_sync(0xFFFFFFFFu, pre_s, o);
+        if (lane >= o) { pre_p += tp; pre_s += ts; }
+    }
+    const int tot_p = __shfl_sync(0xFFFFFFFFu, pre_p, 31);
+    const int tot_s = __shfl_sync(0xFFFFFFFFu, pre_s, 31);
+    unsigned long long bp = 0, bs = 0;
+    if (lane == 31) {
+        if (tot_p) bp = atomicAdd(a.ocount, (unsigned long long)tot_p);
+        if (tot_s) bs = atomicAdd(a.scount, (unsigned long long)tot_s);
+    }
+    bp = __shfl_sync(0xFFFFFFFFu, bp, 31) + (unsigned long long)(pre_p - nprod);
+    bs = __shfl_sync(0xFFFFFFFFu, bs, 31) + (unsigned long long)(pre_s - nspawn);
+    if (!valid) return;
+    const T pm = sqrt(fma(px, px, fma(py, py, pz * pz)));
+    const T inv_pm = pm > (T)0 ? (T)1 / pm : (T)0;
+    const T nx = px * inv_pm, ny = py * inv_pm, nz = pz * inv_pm;
+    if (photon) {
+        // pair creation: the photon is removed, two leptons along its direction
+        const T pme = lepton_pmag(xa * e.g, c), pmp = lepton_pmag(xb * e.g, c);
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const unsigned long long j = bp + m;
+            const T pmag = m == 0 ? pme : pmp;
+            if (j < (unsigned long long)a.cap) {
+                a.opx[j] = nx * pmag; a.opy[j] = ny * pmag; a.opz[j] = nz * pmag;
+                a.opid[j] = id;
+                a.ostep[j] = a.step;
+                a.ometa[j] = (uint8_t)((m == 0 ? SFQ_ELECTRON : SFQ_POSITRON) | ((m + 1) << 2) | (tag << 4));
+            } else {
+                ++c.v[C_DROP];
+            }
+            if (nspawn) {
+                const unsigned long long s = bs + m;
+                if (s < (unsigned long long)a.scap) {
+                    a.spx[s] = nx * pmag; a.spy[s] = ny * pmag; a.spz[s] = nz * pmag;
+                    a.stau[s] = -1.0;
+                    a.sid[s] = id;
+                    a.sflags[s] = (uint8_t)(SFQ_ALIVE | SFQ_JUST_CREATED |
+                                            ((m == 0 ? SFQ_ELECTRON : SFQ_POSITRON) << SFQ_SPECIES_SHIFT) |
+                                            ((m + 1) << SFQ_TAG_SHIFT));
+                    if (a.sfp[0]) {
+#pragma unroll
+                        for (int d3 = 0; d3 < 3; ++d3) { a.sfp[d3][s] = (T)0; a.sdf[d3][s] = (T)0; }
+                    }
+                    if (a.sk0) a.sk0[s] = a.k0[e.i];
+                    if (a.samp) a.samp[s] = a.amp ? a.amp[e.i] : a.amp0;
+                } else {
+                    ++c.v[C_SDROP];
+                }
+            }
+        }
+        a.flags[e.i] = (uint8_t)(fl & ~SFQ_ALIVE);
+    } else {
+        // photon emission: xi = s/(1+s) to the photon, the lepton keeps gamma/(1+s)
+        const T s = xa;
+        const T inv1s = (T)1 / ((T)1 + s);
+        const T gph = e.g * s * inv1s;
+        const T pnew = lepton_pmag(e.g * inv1s, c);
+        const unsigned long long j = bp;
+        if (j < (unsigned long long)a.cap) {
+            a.opx[j] = nx * gph; a.opy[j] = ny * gph; a.opz[j] = nz * gph;
+            a.opid[j] = id;
+            a.ostep[j] = a.step;
+            a.ometa[j] = (uint8_t)(SFQ_PHOTON | (tag << 4));
+        } else {
+            ++c.v[C_DROP];
+        }
+        a.px[e.i] = nx * pnew; a.py[e.i] = ny * pnew; a.pz[e.i] = nz * pnew;
+        a.tau[e.i] = to_tau<T>(fresh_tau(xb));                  // fresh optical depth, word 0 (Sec. 2)
+    }
+}
+
+// T: float (mixed) or double; FK: field source; PPT: particles per lane per chunk.
+// Each warp streams chunks of 32*PPT particles and compacts event lanes into a
+// warp-private ring in shared memory; a full batch of 32 events is sampled by the
+// whole warp.  No block-wide barrier inside the loop.
 template <typename T, int FK, int PPT>
-__global__ void __launch_bounds__(STEP_BS) mc_step_kernel(const StepArgs<T> a) {
-    constexpr int TILE = STEP_BS * PPT;
+__global__ void __launch_bounds__(STEP_BS, SFQ_STEP_MINB) mc_step_kernel(const StepArgs<T> a) {
     using Q = L<T>;
-    __shared__ T s_nlc[Q::RATE_NLC_N];
-    __shared__ T s_nbw[Q::RATE_NBW_N];
-    __shared__ QEntry<T> q[TILE];
-    __shared__ int q_n, q_prod, q_spawn;
-    __shared__ unsigned long long q_pbase, q_sbase;
+    constexpr int WARPS = STEP_BS / 32;
+    constexpr int QS = (32 * (PPT + 1) <= 64) ? 64 : ((32 * (PPT + 1) <= 128) ? 128 : 256);
+    using RS = RateSmem<T>;
+    __shared__ __align__(16) T s_nlc[RS::NLC_N];
+    __shared__ __align__(16) T s_nbw[RS::NBW_N];
+    __shared__ QEntry<T> wq[WARPS][QS];
 
-    for (int k = threadIdx.x; k < Q::RATE_NLC_N; k += STEP_BS) s_nlc[k] = a.tab.nlc_rate[k];
-    for (int k = threadIdx.x; k < Q::RATE_NBW_N; k += STEP_BS) s_nbw[k] = a.tab.nbw_rate[k];
+    stage_rate_table<T, Q::NLC_DEG, RS::NLC_STRIDE>(s_nlc, a.tab.nlc_rate, Q::RATE_NLC_N / (Q::NLC_DEG + 1),
+                                                     threadIdx.x, STEP_BS);
+    stage_rate_table<T, Q::NBW_DEG, RS::NBW_STRIDE>(s_nbw, a.tab.nbw_rate, Q::RATE_NBW_N / (Q::NBW_DEG + 1),
+                                                     threadIdx.x, STEP_BS);
+    __syncthreads();
 
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    QEntry<T> *q = wq[warp];
+    unsigned head = 0, tail = 0;            // warp-uniform ring indices
     Cnt c;
     c.zero();
-    const int64_t ntiles = (a.n + TILE - 1) / TILE;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        if (threadIdx.x == 0) { q_n = 0; q_prod = 0; q_spawn = 0; }
-        __syncthreads();
-        const int64_t base = tile * TILE;
-
-        // ---------------- phase A: rate and event test for every particle
+    constexpr int CH = 32 * PPT;
+    const int64_t nchunks = (a.n + CH - 1) / CH;
+    const int64_t gw = (int64_t)blockIdx.x * WARPS + warp, nw = (int64_t)gridDim.x * WARPS;
+    for (int64_t ch = gw; ch < nchunks; ch += nw) {
+        const int64_t base = ch * CH;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-            const int lidx = k * STEP_BS + threadIdx.x;
-            const int64_t i = base + lidx;
-            if (i >= a.n) continue;
-            const uint8_t fl = a.flags[i];
-            if (!(fl & SFQ_ALIVE)) continue;
-            const T px = a.px[i], py = a.py[i], pz = a.pz[i];
-            T E[3], B[3];
-            load_fields<T, FK>(a, i, E, B);
-            const bool photon = ((fl >> SFQ_SPECIES_SHIFT) & 3) == SFQ_PHOTON;
-            const T p2 = fma(px, px, fma(py, py, pz * pz));
-            const T g = photon ? sqrt(p2) : sqrt((T)1 + p2);
-            const T chi = chi_of<T>(g, px, py, pz, E, B, a.inv_rho);
-            ++c.v[C_UPD];
-            bool oor = false;
-            T d;
-            if (!(chi >= (T)0) || !(g > (T)0)) {
-                ++c.v[C_NAN];
-                d = (T)0;
-            } else if (photon) {
-                d = a.prefdt * wtilde_pair<T>(s_nbw, chi, oor) / g;
-            } else {
-                d = a.prefdt * (chi / g) * wtilde_rad<T>(s_nlc, chi, oor);
-            }
-            c.v[C_OOR] += oor;
-            c.v[C_RDT] += d > (T)0.1;
-            const uint64_t id = a.id ? a.id[i] : a.id_base + (uint64_t)i;
-            const uint32_t tag = (fl >> SFQ_TAG_SHIFT) & 3u;
-            if (od_update(a.tau + i, d, a.seed, id, a.step, tag)) {
-                const int slot = atomicAdd(&q_n, 1);
-                QEntry<T> e;
-                e.lidx = lidx;
-                e.g = g;
-                e.a = chi;
-                e.b = (T)0;
-                q[slot] = e;
-            }
-        }
-        __syncthreads();
-
-        // ---------------- phase B1: sampling on the compacted queue
-        const int nq = q_n;
-        for (int k = threadIdx.x; k < nq; k += STEP_BS) {
-            QEntry<T> e = q[k];
-            const int64_t i = base + e.lidx;
-            const uint8_t fl = a.flags[i];
-            const uint64_t id = a.id ? a.id[i] : a.id_base + (uint64_t)i;
-            const u4 w = draws(a.seed, id, a.step, (fl >> SFQ_TAG_SHIFT) & 3u);
-            const T r1 = uniform<T>(w.w[1]);
-            bool oor = false;
-            ++c.v[C_EV];
-            if (((fl >> SFQ_SPECIES_SHIFT) & 3) == SFQ_PHOTON) {
-                T xe, xp;
-                pair_shares<T>(a.tab.nbw_inv, e.a, r1, xe, xp, oor);
-                e.a = xe;
-                e.b = xp;
-                e.o_prod = (uint16_t)atomicAdd(&q_prod, 2);
-                e.o_spawn = a.scount ? (uint16_t)atomicAdd(&q_spawn, 2) : (uint16_t)0;
-                ++c.v[C_PAIR];
-            } else {
-                e.a = photon_s<T>(a.tab.nlc_inv, e.a, r1, oor);
-                e.o_prod = (uint16_t)atomicAdd(&q_prod, 1);
-                ++c.v[C_EMIT];
-            }
-            c.v[C_OOR] += oor;
-            q[k] = e;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            q_pbase = q_prod ? atomicAdd(a.ocount, (unsigned long long)q_prod) : 0ull;
-            q_sbase = (q_spawn && a.scount) ? atomicAdd(a.scount, (unsigned long long)q_spawn) : 0ull;
-        }
-        __syncthreads();
-
-        // ---------------- phase B2: parents and product records
-        for (int k = threadIdx.x; k < nq; k += STEP_BS) {
-            const QEntry<T> e = q[k];
-            const int64_t i = base + e.lidx;
-            const uint8_t fl = a.flags[i];
-            const uint64_t id = a.id ? a.id[i] : a.id_base + (uint64_t)i;
-            const uint32_t tag = (fl >> SFQ_TAG_SHIFT) & 3u;
-            const T px = a.px[i], py = a.py[i], pz = a.pz[i];
-            const T pm = sqrt(fma(px, px, fma(py, py, pz * pz)));
-            const T inv_pm = pm > (T)0 ? (T)1 / pm : (T)0;
-            const T nx = px * inv_pm, ny = py * inv_pm, nz = pz * inv_pm;
-            if (((fl >> SFQ_SPECIES_SHIFT) & 3) == SFQ_PHOTON) {
-                // pair creation: the photon is removed, two leptons along its direction
-                const T ge = e.a * e.g, gp = e.b * e.g;
-                const T pme = lepton_pmag(ge, c), pmp = lepton_pmag(gp, c);
-                for (int m = 0; m < 2; ++m) {
-                    const unsigned long long j = q_pbase + e.o_prod + m;
-                    const T pmag = m == 0 ? pme : pmp;
-                    if (j < (unsigned long long)a.cap) {
-                        a.opx[j] = nx * pmag; a.opy[j] = ny * pmag; a.opz[j] = nz * pmag;
-                        a.opid[j] = id;
-                        a.ostep[j] = a.step;
-                        a.ometa[j] = (uint8_t)((m == 0 ? SFQ_ELECTRON : SFQ_POSITRON) | ((m + 1) << 2) | (tag << 4));
+            const int64_t i = base + k * 32 + lane;
+            bool ev = false;
+            T g = (T)0, chi = (T)0;
+            if (i < a.n) {
+                const uint8_t fl = a.flags[i];
+                if (fl & SFQ_ALIVE) {
+                    const T px = a.px[i], py = a.py[i], pz = a.pz[i];
+                    T E[3], B[3];
+                    load_fields<T, FK>(a, i, E, B);
+                    const bool photon = ((fl >> SFQ_SPECIES_SHIFT) & 3) == SFQ_PHOTON;
+                    const T p2 = fma(px, px, fma(py, py, pz * pz));
+                    g = photon ? sqrt(p2) : sqrt((T)1 + p2);
+                    chi = chi_of<T>(g, px, py, pz, E, B, a.inv_rho);
+                    ++c.v[C_UPD];
+                    bool oor = false;
+                    T d;
+                    if (!(chi >= (T)0) || !(g > (T)0)) {
+                        ++c.v[C_NAN];
+                        d = (T)0;
+                    } else if (photon) {
+                        d = a.prefdt * wtilde_pair<T>(s_nbw, chi, oor) / g;
                     } else {
-                        ++c.v[C_DROP];
+                        d = a.prefdt * (chi / g) * wtilde_rad<T>(s_nlc, chi, oor);
                     }
-                    if (a.scount) {
-                        const unsigned long long s = q_sbase + e.o_spawn + m;
-                        if (s < (unsigned long long)a.scap) {
-                            a.spx[s] = nx * pmag; a.spy[s] = ny * pmag; a.spz[s] = nz * pmag;
-                            a.stau[s] = -1.0;
-                            a.sid[s] = id;
-                            a.sflags[s] = (uint8_t)(SFQ_ALIVE | SFQ_JUST_CREATED |
-                                                    ((m == 0 ? SFQ_ELECTRON : SFQ_POSITRON) << SFQ_SPECIES_SHIFT) |
-                                                    ((m + 1) << SFQ_TAG_SHIFT));
-                            if (a.sfp[0]) {
-#pragma unroll
-                                for (int d3 = 0; d3 < 3; ++d3) { a.sfp[d3][s] = (T)0; a.sdf[d3][s] = (T)0; }
-                            }
-                            if (a.sk0) a.sk0[s] = a.k0[i];
-                            if (a.samp) a.samp[s] = a.amp ? a.amp[i] : a.amp0;
-                        } else {
-                            ++c.v[C_SDROP];
-                        }
-                    }
+                    c.v[C_OOR] += oor;
+                    c.v[C_RDT] += d > (T)0.1;
+                    const auto id_of = [&]() { return a.id ? a.id[i] : a.id_base + (uint64_t)i; };
+                    ev = od_update(a.tau + i, d, a.seed, id_of, a.step, (fl >> SFQ_TAG_SHIFT) & 3u);
                 }
-                a.flags[i] = (uint8_t)(fl & ~SFQ_ALIVE);
-            } else {
-                // photon emission: xi = s/(1+s) to the photon, the lepton keeps gamma/(1+s)
-                const T s = e.a;
-                const T inv1s = (T)1 / ((T)1 + s);
-                const T gph = e.g * s * inv1s;
-                const T pnew = lepton_pmag(e.g * inv1s, c);
-                const unsigned long long j = q_pbase + e.o_prod;
-                if (j < (unsigned long long)a.cap) {
-                    a.opx[j] = nx * gph; a.opy[j] = ny * gph; a.opz[j] = nz * gph;
-                    a.opid[j] = id;
-                    a.ostep[j] = a.step;
-                    a.ometa[j] = (uint8_t)(SFQ_PHOTON | (tag << 4));
-                } else {
-                    ++c.v[C_DROP];
-                }
-                a.px[i] = nx * pnew; a.py[i] = ny * pnew; a.pz[i] = nz * pnew;
-                // fresh optical depth from word 0 (Sec. 2)
-                const u4 w = draws(a.seed, id, a.step, tag);
-                a.tau[i] = to_tau<T>(fresh_tau(uniform<T>(w.w[0])));
             }
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, ev);
+            if (ev) {
+                const unsigned r = __popc(m & ((1u << lane) - 1u));
+                QEntry<T> e;
+                e.i = i;
+                e.g = g;
+                e.chi = chi;
+                q[(tail + r) & (QS - 1)] = e;
+            }
+            tail += __popc(m);
         }
-        __syncthreads();
+        __syncwarp();
+        while (tail - head >= 32u) {
+            const QEntry<T> e = q[(head + lane) & (QS - 1)];
+            __syncwarp();
+            head += 32;
+            process_events<T>(a, e, true, c);
+        }
+    }
+    // drain the partial batch
+    __syncwarp();
+    if (tail != head) {
+        const unsigned nv = tail - head;
+        QEntry<T> e = q[(head + lane) & (QS - 1)];
+        process_events<T>(a, e, (unsigned)lane < nv, c);
     }
     flush_counters(c, a.counters);
 }

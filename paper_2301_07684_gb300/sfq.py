@@ -15,7 +15,7 @@ import os
 import torch
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libsfq.so")
+LIB_PATH = os.environ.get("SFQ_LIB", os.path.join(_PKG, "libsfq.so"))
 
 SFQ_FP32, SFQ_FP64 = 0, 1
 SFQ_ALIVE, SFQ_JUST_CREATED = 1, 2
@@ -26,7 +26,7 @@ SFQ_FIELDS_SOA, SFQ_FIELDS_PLANE_WAVE = 0, 1
 STATUS = {0: "SFQ_OK", 1: "SFQ_ERR_ARG", 2: "SFQ_ERR_CUDA", 3: "SFQ_ERR_CAPACITY", 4: "SFQ_ERR_TABLE",
           5: "SFQ_ERR_RANGE", 6: "SFQ_ERR_TIMEOUT"}
 COUNTER_NAMES = ["updates", "events", "emitted", "pairs", "dropped", "spawn_dropped", "out_of_range",
-                 "nan_input", "gamma_below_one", "large_rdt", "blcfa_no_emission", "blcfa_rejected"]
+                 "nan_input", "gamma_below_one", "large_rdt", "blcfa_no_emission", "blcfa_rejected", "timeouts"]
 
 
 class Config(C.Structure):
@@ -86,13 +86,16 @@ def lib():
         L.sfq_mc_step.argtypes = [vp, C.POINTER(Particles), C.POINTER(Fields), u32, C.POINTER(Products),
                                   C.POINTER(Spawn), vp, vp]
         L.sfq_mc_step.restype = st
+        L.sfq_set_step_shape.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
+        L.sfq_set_step_shape.restype = st
         L.sfq_version.restype = C.c_char_p
         _lib = L
     return _lib
 
 
 EXPORTED = ["sfq_init", "sfq_finalize", "sfq_last_error", "sfq_constants", "sfq_photon_rate", "sfq_pair_rate",
-            "sfq_uniforms", "sfq_sample_photon_xi", "sfq_sample_pair_xi", "sfq_mc_step", "sfq_version"]
+            "sfq_uniforms", "sfq_sample_photon_xi", "sfq_sample_pair_xi", "sfq_mc_step", "sfq_set_step_shape",
+            "sfq_version"]
 
 
 def _ptr(t):
@@ -158,6 +161,10 @@ class Context:
         if t.dtype != self.dtype or not t.is_cuda or not t.is_contiguous():
             raise SfqError(f"{name}: expected a contiguous CUDA {self.dtype} tensor")
         return t
+
+    def set_step_shape(self, variant=0, ppt=0, grid_blocks=0):
+        """variant 0 = automatic, 1 = warp-streaming kernel, 2 = TMA-staged kernel."""
+        self._check(lib().sfq_set_step_shape(self._h, variant, ppt, grid_blocks), "sfq_set_step_shape")
 
     # --- entry points -------------------------------------------------------
     def photon_rate(self, gamma, chi, out=None, counters=None):

@@ -32,10 +32,11 @@ def _np_dtype(precision):
     return np.float32 if precision == "fp32" else np.float64
 
 
-def run_gpu(ctx, d, nsteps, field_mode, products_cap, step0=0):
+def run_gpu(ctx, d, nsteps, field_mode, products_cap, step0=0, variant=0, ppt=0):
     import torch
     from paper_2301_07684_gb300 import sfq
     dev = ctx.device
+    ctx.set_step_shape(variant, ppt, 0)
     T = lambda a, dt=None: torch.as_tensor(np.ascontiguousarray(a)).to(dev) if dt is None else \
         torch.as_tensor(np.ascontiguousarray(a)).to(device=dev, dtype=dt)
     n = d["px"].size
@@ -47,12 +48,16 @@ def run_gpu(ctx, d, nsteps, field_mode, products_cap, step0=0):
     cnt = sfq.counters_tensor()
     z = torch.zeros(n, dtype=ctx.dtype, device=dev)
     ey = torch.empty(n, dtype=ctx.dtype, device=dev)
+    k0_64 = T(d["k0"].astype(np.int64))
+    K = d["table"].size
+    amp_t = amp if amp is not None else torch.tensor(d["amp0"], dtype=ctx.dtype, device=dev)
     for s in range(step0, step0 + nsteps):
         if field_mode == "pw":
             F = sfq.FieldSource.plane_wave(k0, table, d["k_step"], amp=amp, amp0=d.get("amp0", 0.0))
         else:
-            E, B = W.plane_wave_fields(d["k0"], d["amp"] if "amp" in d else d["amp0"], d["table"], s)
-            ey.copy_(T(E[1]))
+            # E_y = B_z = amp * table[(k0 + s k_step) mod K]: one rounded product, as the host generator forms it
+            idx = (k0_64 + (s * d["k_step"]) % K) % K
+            torch.mul(amp_t, table[idx], out=ey)
             F = sfq.FieldSource.soa(z, ey, z, z, z, ey)
         ctx.mc_step(P, F, s, out, counters=cnt)
     torch.cuda.synchronize()
@@ -86,14 +91,17 @@ def gpu_subset(P, out, ids):
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 @pytest.mark.parametrize("field_mode", ["soa", "pw"])
-def test_config2_small(oracle, precision, field_mode):
+@pytest.mark.parametrize("variant,ppt", [(1, 0), (2, 0), (2, 4)], ids=["warp", "tma16", "tma8"])
+def test_config2_small(oracle, precision, field_mode, variant, ppt):
+    """Both kernels (warp-streaming and TMA-staged, whose last tile is partial here)."""
     ctx = _ctx(precision)
     n, nsteps = 16384 + 77, 60
     d = W.config2(n=n, seed=0, dtype=_np_dtype(precision))
-    P, out, cnt = run_gpu(ctx, d, nsteps, field_mode, products_cap=8 * n)
+    P, out, cnt = run_gpu(ctx, d, nsteps, field_mode, products_cap=8 * n, variant=variant, ppt=ppt)
     from paper_2301_07684_gb300 import sfq
     c = sfq.counters_dict(cnt)
     assert c["updates"] == n * nsteps and c["dropped"] == 0 and c["out_of_range"] == 0
+    assert c["timeouts"] == 0
     assert out.n() == c["emitted"] == c["events"]
     ids = W.sample_ids(n, 128, seed=3)
     ids = np.unique(np.concatenate([ids, [0, n - 1, n - 77]]))
@@ -128,9 +136,9 @@ def test_config2_full_size(oracle):
     ctx = _ctx("fp32")
     d = W.config2(n=1 << 24, seed=0)
     n, nsteps = d["px"].size, d["nsteps"]
-    P, out, cnt = run_gpu(ctx, d, nsteps, "pw", products_cap=int(16 * n))
+    P, out, cnt = run_gpu(ctx, d, nsteps, "soa", products_cap=int(16 * n))
     c = sfq.counters_dict(cnt)
-    assert c["updates"] == n * nsteps and c["dropped"] == 0
+    assert c["updates"] == n * nsteps and c["dropped"] == 0 and c["timeouts"] == 0
     ids = W.sample_ids(n, 48, seed=11)
     orc = oracle_lineages(oracle, d, ids, nsteps, ctx.rho, ctx.seed, NEAR["fp32"])
     final, prod = gpu_subset(P, out, ids)
