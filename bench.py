@@ -62,7 +62,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "10"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -261,7 +261,9 @@ def run_ours(args):
                        "precision": "fp32-mixed", "l2": "inputs larger than L2 (~760 MB read per step)",
                        "parallelism": f"dp{world} (independent particles, no collective)"},
             "roofline": {"bound": "hbm", "achieved": main["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
-                         "frac": main["frac"], "traffic": None, "peak_source": peak_src,
+                         "frac": main["frac"],
+                         "traffic": (args.traffic_per_update * n if args.traffic_per_update else None),
+                         "peak_source": peak_src,
                          "bytes_per_update": main["bytes_per_update"]},
             "cpu_baseline": cpu,
             "e2e": main["e2e"],
@@ -315,7 +317,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    per_step = args.oracle_particles
+    per_step = max(16, args.oracle_particles // 8)
     for s in range(args.warmup):
         oracle_sample_run(per_step, 1, step0=s)
     tot_upd, tot_sec, thr = 0, 0.0, 1
@@ -338,12 +340,14 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_PARTICLES)
-    ap.add_argument("--oracle-particles", type=int, default=48)
-    ap.add_argument("--oracle-steps", type=int, default=40)
+    ap.add_argument("--oracle-particles", type=int, default=512)
+    ap.add_argument("--oracle-steps", type=int, default=50)
+    ap.add_argument("--traffic-per-update", type=float, default=None,
+                    help="DRAM bytes per update of the step kernel from an ncu capture (for roofline.traffic)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":

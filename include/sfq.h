@@ -140,6 +140,9 @@ typedef struct {
     void *dfprev[3];          /* real[n] each: BLCFA F_perp^(n-1) - F_perp^(n-2) (in/out) */
     int32_t lepton_model;     /* SFQ_LEPTON_LCFA_OD or SFQ_LEPTON_BLCFA_LOCAL */
     int32_t reserved;
+    const unsigned long long *n_dev;  /* optional device count: the step covers min(*n_dev, n)
+                                         particles (a population grown on the device, e.g. the
+                                         children of sfq_spawn); NULL = n */
 } sfq_particles;
 
 enum { SFQ_FIELDS_SOA = 0, SFQ_FIELDS_PLANE_WAVE = 1 };
@@ -219,8 +222,9 @@ sfq_status sfq_mc_step(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f
  *   variant: 0 = automatic; 1 = warp-streaming kernel (each warp loads its particles
  *            directly); 2 = TMA-staged kernel (bulk copies of each tile into shared
  *            memory, one persistent block per SM).
- *   ppt:     particles per lane per chunk of the warp-streaming kernel (1, 2 or 4;
- *            0 = default).
+ *   ppt:     shape of the chosen kernel: particles per lane per chunk of the
+ *            warp-streaming kernel (1, 2 or 4), or consumer warps per block of the
+ *            TMA-staged kernel (8, 16 or 20); 0 = default.
  *   grid_blocks: grid size (0 = one wave of resident blocks on every SM).
  * Returns SFQ_ERR_ARG for other values.  Results do not depend on the shape. */
 sfq_status sfq_set_step_shape(sfq_ctx *ctx, int32_t variant, int32_t ppt, int32_t grid_blocks);

@@ -115,6 +115,7 @@ static double integrate(orc_fn f, const void *ctx, double a, double b, double re
             if (P[i].e > emax) { emax = P[i].e; imax = i; }
         }
         sum = R;
+        if (E != E || R != R) break;                 /* NaN integrand: no refinement helps */
         if (E <= rel * fabs(R) || E == 0.0 || np >= GK_MAXP - 1) break;
         gk_panel *q = &P[imax];
         const double m = 0.5 * (q->a + q->b);
@@ -692,7 +693,8 @@ static void step_photon(orc_state *s, const double E[3], const double B[3], uint
             c->p[0] = pc[0]; c->p[1] = pc[1]; c->p[2] = pc[2];
             c->tau = -1.0; c->tau0 = 0.0;
             c->id = s->id; c->tag = (uint32_t)(m + 1);
-            c->flags = FL_ALIVE | FL_JUST_CREATED;
+            /* a lepton created without momentum does not take part in later steps */
+            c->flags = (uint8_t)((pc[0] != 0.0 || pc[1] != 0.0 || pc[2] != 0.0 ? FL_ALIVE : 0) | FL_JUST_CREATED);
             c->species = (uint8_t)(m == 0 ? SP_ELECTRON : SP_POSITRON);
         }
     }
@@ -706,9 +708,13 @@ static void emit_photon(orc_state *s, double gamma, double su, uint32_t n, orc_p
     const double gnew = gamma / (1.0 + su);                     /* (1 - xi) gamma_e */
     double pph[3], pnew[3];
     collinear(nh, gph, pph);                                    /* photon: |p| = gamma */
-    collinear(nh, lepton_pmag(gnew), pnew);
+    const double pm_new = lepton_pmag(gnew);
+    collinear(nh, pm_new, pnew);
     push_product(sink, pph, s->id, n, s->tag, SP_PHOTON, 0);
     s->p[0] = pnew[0]; s->p[1] = pnew[1]; s->p[2] = pnew[2];
+    /* READING: a lepton left without momentum is outside the ultrarelativistic regime the
+     * rates assume (Sec. 4) and has no direction for collinear emission: it leaves the step */
+    if (!(pm_new > 0.0)) s->flags &= (uint8_t)~FL_ALIVE;
 }
 
 /* One step of a lepton, LCFA emission by the optical-depth method. */

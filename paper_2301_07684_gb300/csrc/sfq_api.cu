@@ -85,10 +85,12 @@ sfq_status sfq_init(const sfq_config *cfg, sfq_ctx **out) {
     if (e != cudaSuccess) { delete ctx; return SFQ_ERR_CUDA; }
     ctx->num_sms = prop.multiProcessorCount;
     const sfq::HostTables t = sfq::host_tables(cfg->precision);
-    const void *src[4] = {t.nlc_rate, t.nbw_rate, t.nlc_inv, t.nbw_inv};
-    const size_t bytes[4] = {t.nlc_rate_bytes, t.nbw_rate_bytes, t.nlc_inv_bytes, t.nbw_inv_bytes};
-    void **dst[4] = {&ctx->d_nlc_rate, &ctx->d_nbw_rate, &ctx->d_nlc_inv, &ctx->d_nbw_inv};
-    for (int k = 0; k < 4; ++k) {
+    const void *src[6] = {t.nlc_rate, t.nbw_rate, t.nlc_inv, t.nbw_inv, t.k23, t.ki13};
+    const size_t bytes[6] = {t.nlc_rate_bytes, t.nbw_rate_bytes, t.nlc_inv_bytes, t.nbw_inv_bytes, t.k23_bytes,
+                             t.ki13_bytes};
+    void **dst[6] = {&ctx->d_nlc_rate, &ctx->d_nbw_rate, &ctx->d_nlc_inv, &ctx->d_nbw_inv, &ctx->d_k23,
+                     &ctx->d_ki13};
+    for (int k = 0; k < 6; ++k) {
         if (!src[k] || bytes[k] == 0) { sfq_finalize(ctx); return SFQ_ERR_TABLE; }
         e = cudaMalloc(dst[k], bytes[k]);
         if (e == cudaSuccess) e = cudaMemcpy(*dst[k], src[k], bytes[k], cudaMemcpyHostToDevice);
@@ -102,7 +104,7 @@ void sfq_finalize(sfq_ctx *ctx) {
     if (!ctx) return;
     {
         DeviceGuard g(ctx->device);
-        void *ptrs[4] = {ctx->d_nlc_rate, ctx->d_nbw_rate, ctx->d_nlc_inv, ctx->d_nbw_inv};
+        void *ptrs[6] = {ctx->d_nlc_rate, ctx->d_nbw_rate, ctx->d_nlc_inv, ctx->d_nbw_inv, ctx->d_k23, ctx->d_ki13};
         for (void *p : ptrs)
             if (p) cudaFree(p);
     }
@@ -189,8 +191,14 @@ sfq_status sfq_mc_step(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f
     if (!ctx) return SFQ_ERR_ARG;
     if (!p || !f || !out) return fail(ctx, SFQ_ERR_ARG, "null descriptor");
     if (p->n < 0 || out->capacity < 0) return fail(ctx, SFQ_ERR_ARG, "negative size");
-    if (p->lepton_model != SFQ_LEPTON_LCFA_OD)
-        return fail(ctx, SFQ_ERR_ARG, "lepton model not available in this build");
+    if (p->lepton_model != SFQ_LEPTON_LCFA_OD && p->lepton_model != SFQ_LEPTON_BLCFA_LOCAL)
+        return fail(ctx, SFQ_ERR_ARG, "unknown lepton model");
+    if (p->lepton_model == SFQ_LEPTON_BLCFA_LOCAL && p->n > 0) {
+        for (int k = 0; k < 3; ++k)
+            if (!p->fprev[k] || !p->dfprev[k] || !aligned16(p->fprev[k]) || !aligned16(p->dfprev[k]))
+                return fail(ctx, SFQ_ERR_ARG, "beyond-LCFA state arrays null or misaligned");
+    }
+    if (p->n_dev && !aligned8(p->n_dev)) return fail(ctx, SFQ_ERR_ARG, "n_dev misaligned");
     if (p->n == 0) return SFQ_OK;
     const void *need16[] = {p->px, p->py, p->pz, p->tau, p->flags};
     for (const void *q : need16)
@@ -235,7 +243,9 @@ sfq_status sfq_mc_step(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f
 sfq_status sfq_set_step_shape(sfq_ctx *ctx, int32_t variant, int32_t ppt, int32_t grid_blocks) {
     if (!ctx) return SFQ_ERR_ARG;
     if (variant < 0 || variant > 2) return fail(ctx, SFQ_ERR_ARG, "variant must be 0, 1 or 2");
-    if (!(ppt == 0 || ppt == 1 || ppt == 2 || ppt == 4)) return fail(ctx, SFQ_ERR_ARG, "ppt must be 0, 1, 2 or 4");
+    const bool ok = variant == 2 ? (ppt == 0 || ppt == 8 || ppt == 16 || ppt == 20)
+                                 : (ppt == 0 || ppt == 1 || ppt == 2 || ppt == 4);
+    if (!ok) return fail(ctx, SFQ_ERR_ARG, "shape: 1, 2 or 4 particles per lane (variant 1), 8/16/20 warps (variant 2)");
     if (grid_blocks < 0) return fail(ctx, SFQ_ERR_ARG, "grid_blocks < 0");
     ctx->step_variant = variant;
     ctx->step_ppt = ppt;

@@ -12,7 +12,7 @@ struct sfq_ctx {
     int device;
     double rho, pref;
     // device copies of the fitted tables (one precision per context)
-    void *d_nlc_rate, *d_nbw_rate, *d_nlc_inv, *d_nbw_inv;
+    void *d_nlc_rate, *d_nbw_rate, *d_nlc_inv, *d_nbw_inv, *d_k23, *d_ki13;
     int num_sms;
     int step_variant = 0;    // 0 = automatic, 1 = warp-streaming, 2 = TMA-staged
     int step_ppt = 0;        // 0 = default
@@ -69,8 +69,8 @@ cudaError_t launch_step_f64(const StepLaunch &);
 
 // Host copies of the tables (sfq_tables_host.cu).
 struct HostTables {
-    const void *nlc_rate, *nbw_rate, *nlc_inv, *nbw_inv;
-    size_t nlc_rate_bytes, nbw_rate_bytes, nlc_inv_bytes, nbw_inv_bytes;
+    const void *nlc_rate, *nbw_rate, *nlc_inv, *nbw_inv, *k23, *ki13;
+    size_t nlc_rate_bytes, nbw_rate_bytes, nlc_inv_bytes, nbw_inv_bytes, k23_bytes, ki13_bytes;
 };
 HostTables host_tables(int precision);
 

@@ -40,6 +40,10 @@ template <typename T> struct L;
         static constexpr int PP_YE0 = NBW_INV_##P##_Y_ELO, PP_YSUB = NBW_INV_##P##_Y_SUB,         \
                              PP_YSUBLOW = NBW_INV_##P##_Y_SUBLOW, PP_YQLO = NBW_INV_##P##_Y_QLO,  \
                              PP_YSUBQ = NBW_INV_##P##_Y_SUBQ, PP_NY = NBW_INV_##P##_Y_NPIECES;    \
+        static constexpr int K23_DEG = K23_##P##_DEG, K23_ELO = K23_##P##_X_ELO, K23_EHI = K23_##P##_X_EHI, \
+                             K23_SUB = K23_##P##_X_SUB;                                            \
+        static constexpr int KI13_DEG = KI13_##P##_DEG, KI13_ELO = KI13_##P##_X_ELO,             \
+                             KI13_EHI = KI13_##P##_X_EHI, KI13_SUB = KI13_##P##_X_SUB;            \
     };
 SFQ_LAYOUT(float, F32)
 SFQ_LAYOUT(double, F64)
@@ -47,7 +51,7 @@ SFQ_LAYOUT(double, F64)
 
 template <typename T>
 struct Tables {
-    const T *nlc_rate, *nbw_rate, *nlc_inv, *nbw_inv;
+    const T *nlc_rate, *nbw_rate, *nlc_inv, *nbw_inv, *k23, *ki13;
 };
 
 // Rate tables in shared memory: each piece padded to a multiple of 16 bytes so that
@@ -167,6 +171,33 @@ __device__ __forceinline__ void pair_shares(const T *__restrict__ inv, T chi, T 
     const T small = (T)0.5 * y, big = (T)1 - small;
     if (rp >= (T)0) { xe = big; xp = small; }
     else { xe = small; xp = big; }
+}
+
+// ln of the photon spectrum Eq. pe_dp at u = eps_gamma/(eps_e - eps_gamma), without the
+// factor common to both sides of Eq. rej_cond:
+//   S(u) = ((1 + (1+u)^2)/(1+u)) K_2/3(x) - Ki_1/3(x),  x = 2u/(3 chi),
+// with K_2/3(x) = g1(x) x^{-2/3} e^{-x} and Ki_1/3(x) = g2(x) e^{-x} from the fitted g1, g2.
+__device__ __forceinline__ float pow_m23(float x) { return exp2f(-0.666666686534881591796875f * log2f(x)); }
+__device__ __forceinline__ double pow_m23(double x) { return exp2(-(2.0 / 3.0) * log2(x)); }
+template <typename T>
+__device__ __forceinline__ T ln_spectrum(const T *__restrict__ k23, const T *__restrict__ ki13, T u, T chi,
+                                         bool &oor) {
+    using Q = L<T>;
+    const T x = (T)2 * u / ((T)3 * chi);
+    T xl;
+    int p = octave_piece<T, Q::K23_ELO, Q::K23_EHI, Q::K23_SUB, 0, 0>(x, xl, oor);
+    T c1[Q::K23_DEG + 1];
+#pragma unroll
+    for (int k = 0; k <= Q::K23_DEG; ++k) c1[k] = __ldg(k23 + p * (Q::K23_DEG + 1) + k);
+    const T g1 = horner1<Q::K23_DEG>(c1, xl);
+    p = octave_piece<T, Q::KI13_ELO, Q::KI13_EHI, Q::KI13_SUB, 0, 0>(x, xl, oor);
+    T c2[Q::KI13_DEG + 1];
+#pragma unroll
+    for (int k = 0; k <= Q::KI13_DEG; ++k) c2[k] = __ldg(ki13 + p * (Q::KI13_DEG + 1) + k);
+    const T g2 = horner1<Q::KI13_DEG>(c2, xl);
+    const T opu = (T)1 + u;
+    const T g = ((T)1 + opu * opu) / opu * g1 * pow_m23(x) - g2;
+    return log(g) - x;
 }
 
 // ---------------------------------------------------------------------------

@@ -13,6 +13,8 @@ static Tables<T> tables_of(const sfq_ctx *ctx) {
     t.nbw_rate = static_cast<const T *>(ctx->d_nbw_rate);
     t.nlc_inv = static_cast<const T *>(ctx->d_nlc_inv);
     t.nbw_inv = static_cast<const T *>(ctx->d_nbw_inv);
+    t.k23 = static_cast<const T *>(ctx->d_k23);
+    t.ki13 = static_cast<const T *>(ctx->d_ki13);
     return t;
 }
 
@@ -58,7 +60,13 @@ static cudaError_t launch_step_t(const StepLaunch &L) {
     if (p.n == 0) return cudaSuccess;
     StepArgs<T> a{};
     a.n = p.n;
+    a.n_dev = p.n_dev;
     a.px = static_cast<T *>(p.px); a.py = static_cast<T *>(p.py); a.pz = static_cast<T *>(p.pz);
+    for (int k = 0; k < 3; ++k) {
+        a.fprev[k] = static_cast<T *>(p.fprev[k]);
+        a.dfprev[k] = static_cast<T *>(p.dfprev[k]);
+    }
+    a.lepton_model = p.lepton_model;
     a.tau = p.tau;
     a.id = p.id;
     a.id_base = p.id_base;
@@ -98,27 +106,40 @@ static cudaError_t launch_step_t(const StepLaunch &L) {
     a.seed = ctx->cfg.seed;
     a.prefdt = (T)(ctx->pref * ctx->cfg.dt);
     a.inv_rho = (T)(1.0 / ctx->rho);
+    a.rho = (T)ctx->rho;
+    a.inv_dt = (T)(1.0 / ctx->cfg.dt);
+    a.inv_dt2 = (T)(1.0 / (ctx->cfg.dt * ctx->cfg.dt));
     a.tab = tables_of<T>(ctx);
     a.counters = L.counters;
     const bool pw = f.kind == SFQ_FIELDS_PLANE_WAVE;
     // TMA-staged kernel: one persistent block per SM; chosen automatically when every
-    // SM gets at least one full tile
-    constexpr int TILE = TmaStage<T, FK_SOA>::TILE;
-    const bool tma = L.variant == 2 || (L.variant == 0 && p.n >= (int64_t)TILE * ctx->num_sms);
+    // SM gets at least one full tile.  `ppt` selects the consumer warps per block.
+    const int cw = (L.ppt == 8 || L.ppt == 16 || L.ppt == 20) ? L.ppt : 16;
+    const int tile = cw * (sizeof(T) == 4 ? 64 : 32);
+    // the beyond-LCFA model runs on the warp-streaming kernel (its state is read directly)
+    const bool tma = p.lepton_model != SFQ_LEPTON_BLCFA_LOCAL &&
+                     (L.variant == 2 || (L.variant == 0 && p.n >= (int64_t)tile * ctx->num_sms));
     if (tma) {
-        // 16 consumer warps with 1024/16 particles each, or 8 warps with twice as many per lane (ppt = 4)
-        const bool w8 = L.ppt == 4;
-        void (*kern)(const StepArgs<T>) =
-            pw ? (w8 ? mc_step_tma_kernel<T, FK_PW, 8> : mc_step_tma_kernel<T, FK_PW, 16>)
-               : (w8 ? mc_step_tma_kernel<T, FK_SOA, 8> : mc_step_tma_kernel<T, FK_SOA, 16>);
-        const int threads = 32 * ((w8 ? 8 : 16) + 1);
-        const size_t smem = pw ? tma_smem_bytes<T, FK_PW>() : tma_smem_bytes<T, FK_SOA>();
+        void (*kern)(const StepArgs<T>) = nullptr;
+        size_t smem = 0;
+#define SFQ_TMA_CASE(CWV)                                                                             \
+    case CWV:                                                                                         \
+        kern = pw ? mc_step_tma_kernel<T, FK_PW, CWV> : mc_step_tma_kernel<T, FK_SOA, CWV>;             \
+        smem = pw ? tma_smem_bytes<T, FK_PW, CWV>() : tma_smem_bytes<T, FK_SOA, CWV>();                 \
+        break;
+        switch (cw) {
+            SFQ_TMA_CASE(8)
+            SFQ_TMA_CASE(20)
+            default:
+            SFQ_TMA_CASE(16)
+        }
+#undef SFQ_TMA_CASE
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        const int64_t ntiles = (p.n + TILE - 1) / TILE;
+        const int64_t ntiles = (p.n + tile - 1) / tile;
         int grid = L.grid > 0 ? L.grid : ctx->num_sms;
         if (ntiles < grid) grid = (int)ntiles;
-        kern<<<grid, threads, smem, L.stream>>>(a);
+        kern<<<grid, 32 * (cw + 1), smem, L.stream>>>(a);
         return cudaGetLastError();
     }
     void (*kern)(const StepArgs<T>) = nullptr;

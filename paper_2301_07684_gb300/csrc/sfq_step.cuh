@@ -18,11 +18,14 @@ template <typename T>
 struct StepArgs {
     // particles
     int64_t n;
+    const unsigned long long *n_dev;    // optional device count (min with n)
     T *px, *py, *pz;
     double *tau;
     const uint64_t *id;
     uint64_t id_base;
     uint8_t *flags;
+    T *fprev[3], *dfprev[3];            // beyond-LCFA state
+    int lepton_model;
     // fields
     const T *ex, *ey, *ez, *bx, *by, *bz;
     const uint32_t *k0;
@@ -52,6 +55,8 @@ struct StepArgs {
     uint64_t seed;
     T prefdt;        // pref * dt
     T inv_rho;       // 1 / rho
+    T rho;
+    T inv_dt, inv_dt2;
     Tables<T> tab;
     sfq_counters *counters;
 };
@@ -62,6 +67,20 @@ struct QEntry {
     T g;                // energy of the particle
     T chi;              // quantum parameter at the event
 };
+// Entry of the warp-streaming kernel, which also serves beyond-LCFA leptons.
+template <typename T>
+struct QEntryX {
+    int64_t i;
+    T g, chi;
+    T aux;              // -1: optical-depth event; beyond-LCFA: gamma_LCFA (> 0) or 0 (no rejection)
+};
+
+template <typename T>
+__device__ __forceinline__ int64_t effective_n(const StepArgs<T> &a) {
+    if (!a.n_dev) return a.n;
+    const int64_t m = (int64_t)*a.n_dev;
+    return m < a.n ? m : a.n;
+}
 
 constexpr int STEP_BS = 256;
 #ifndef SFQ_STEP_MINB
@@ -148,12 +167,77 @@ __device__ __forceinline__ T lepton_pmag(T g, Cnt &c) {
     return sqrt(q);
 }
 
+// Beyond-LCFA lepton (Sec. 5): force history (Eqs. fl ... condit; no pusher: F_L = E + beta x B,
+// p_L = p), local test R dt > r (Sec. 2, word 0) and the threshold gamma_LCFA (Eq. gammaLCFA,
+// with sinh(3 asinh z) = 3z + 4z^3).  Returns true when an emission is to be sampled; aux is
+// gamma_LCFA when the rejection of Eq. rej_cond applies, 0 when the LCFA spectrum applies.
+template <typename T>
+__device__ __forceinline__ bool blcfa_phase_a(const StepArgs<T> &a, const T *s_nlc, int64_t i, uint8_t fl, T px,
+                                              T py, T pz, const T E[3], const T B[3], T &g, T &chi, T &aux,
+                                              Cnt &c) {
+    const T g2 = fma(px, px, fma(py, py, fma(pz, pz, (T)1)));
+    const T inv_g = rsqrt_nr(g2);
+    g = sqrt_nr(g2);
+    const T bx = px * inv_g, by = py * inv_g, bz = pz * inv_g;
+    const T FL[3] = {E[0] + (by * B[2] - bz * B[1]), E[1] + (bz * B[0] - bx * B[2]), E[2] + (bx * B[1] - by * B[0])};
+    const T fp = (FL[0] * px + FL[1] * py + FL[2] * pz) * inv_g * inv_g;
+    const T F[3] = {FL[0] - fp * px, FL[1] - fp * py, FL[2] - fp * pz};      // Eq. fl_perp
+    const T F2 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
+    chi = g * sqrt_nr(F2) * a.inv_rho;                                       // Eq. chi_p
+    ++c.v[C_UPD];
+    if (fl & SFQ_JUST_CREATED) {
+        // first update after creation: F^(n-2) = F^(n-1) = F^(n), no emission
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { a.fprev[k][i] = F[k]; a.dfprev[k][i] = (T)0; }
+        a.flags[i] = (uint8_t)(fl & ~SFQ_JUST_CREATED);
+        return false;
+    }
+    T d1[3], Fd2 = (T)0, FFdd = (T)0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const T fpv = a.fprev[k][i], dfv = a.dfprev[k][i];
+        d1[k] = F[k] - fpv;
+        const T fd = d1[k] * a.inv_dt;
+        const T fdd = (d1[k] - dfv) * a.inv_dt2;
+        Fd2 = fma(fd, fd, Fd2);
+        FFdd = fma(F[k], fdd, FFdd);
+        a.fprev[k][i] = F[k];
+        a.dfprev[k][i] = d1[k];
+    }
+    const T D = Fd2 + fabs(FFdd);                                            // delta / tau_C^2, Eq. condit
+    // gamma^2 delta/zeta^2 > chi^2 F^2 divided by gamma^2 tau_C^2 > 0, zeta = 2^-52
+    const T zeta = (T)2.220446049250313080847263336181640625e-16;
+    const T zeta2 = (T)4.930380657631323783823303533017413935457540219431393779648e-32;
+    const bool gate = (D > zeta2 * F2 * F2) && (chi > zeta);
+    bool oor = false;
+    const T d = a.prefdt * (chi * inv_g) * wtilde_rad<T>(s_nlc, chi, oor);
+    c.v[C_OOR] += oor;
+    c.v[C_RDT] += d > (T)0.1;
+    const uint64_t id = a.id ? a.id[i] : a.id_base + (uint64_t)i;
+    const u4 w = draws(a.seed, id, a.step, (fl >> SFQ_TAG_SHIFT) & 3u);
+    if (!(d > uniform<T>(w.w[0]))) return false;                            // local test
+    ++c.v[C_EV];
+    aux = (T)0;
+    if (gate) {
+        const T tau_ratio = (T)6.283185307179586476925286766559 * a.rho * sqrt_nr(F2 / D);   // tau / tau_C
+        const T z = chi / ((T)8 * g) * tau_ratio;
+        const T gL = (T)0.7 * g / ((T)1 + (T)4 / ((T)3 * (T)3.1415926535897932384626433832795 * chi) *
+                                              (z * fma((T)4 * z, z, (T)3)));
+        if (!(gL < (T)0.75 * g)) {                                          // no emission (Sec. 5)
+            ++c.v[C_NOEM];
+            return false;
+        }
+        aux = gL;
+    }
+    return true;
+}
+
 // One batch of up to 32 queued events, one per lane (lanes >= nvalid idle); all
 // 32 lanes execute it (warp shuffles).  Sampling (Eq. again / Eq. again_pp),
 // parent update and product records; one global atomic per batch reserves the
 // records.
-template <typename T>
-__device__ __forceinline__ void process_events(const StepArgs<T> &a, const QEntry<T> &e, bool valid, Cnt &c) {
+template <typename T, typename E>
+__device__ __forceinline__ void process_events(const StepArgs<T> &a, const E &e, T e_aux, bool valid, Cnt &c) {
     const int lane = threadIdx.x & 31;
     int nprod = 0, nspawn = 0;
     T px = 0, py = 0, pz = 0, xa = 0, xb = 0;
@@ -170,17 +254,36 @@ __device__ __forceinline__ void process_events(const StepArgs<T> &a, const QEntr
         photon = ((fl >> SFQ_SPECIES_SHIFT) & 3) == SFQ_PHOTON;
         const u4 w = draws(a.seed, id, a.step, tag);
         const T r1 = uniform<T>(w.w[1]);
-        ++c.v[C_EV];
         if (photon) {
+            ++c.v[C_EV];
             pair_shares<T>(a.tab.nbw_inv, e.chi, r1, xa, xb, oor);
             nprod = 2;
             nspawn = a.scount ? 2 : 0;
             ++c.v[C_PAIR];
-        } else {
+        } else if (e_aux < (T)0) {
+            ++c.v[C_EV];
             xa = photon_s<T>(a.tab.nlc_inv, e.chi, r1, oor);      // s
             xb = uniform<T>(w.w[0]);                               // for the fresh optical depth
             nprod = 1;
             ++c.v[C_EMIT];
+        } else {
+            // beyond-LCFA: LCFA sample, then the rejection of Eq. rej_cond below gamma_LCFA
+            xa = photon_s<T>(a.tab.nlc_inv, e.chi, r1, oor);
+            xb = (T)-1;                                            // marks: no optical depth
+            bool accept = true;
+            const T gbar = e.g * xa / ((T)1 + xa);
+            if (e_aux > (T)0 && !(gbar > e_aux)) {
+                const T uL = e_aux / (e.g - e_aux);
+                const T lhs = log(uniform<T>(w.w[2])) + ln_spectrum<T>(a.tab.k23, a.tab.ki13, xa, e.chi, oor);
+                const T rhs = ln_spectrum<T>(a.tab.k23, a.tab.ki13, uL, e.chi, oor);
+                accept = lhs <= rhs;
+            }
+            if (accept) {
+                nprod = 1;
+                ++c.v[C_EMIT];
+            } else {
+                ++c.v[C_REJ];
+            }
         }
         c.v[C_OOR] += oor;
     }
@@ -226,7 +329,7 @@ __device__ __forceinline__ void process_events(const StepArgs<T> &a, const QEntr
                     a.spx[s] = nx * pmag; a.spy[s] = ny * pmag; a.spz[s] = nz * pmag;
                     a.stau[s] = -1.0;
                     a.sid[s] = id;
-                    a.sflags[s] = (uint8_t)(SFQ_ALIVE | SFQ_JUST_CREATED |
+                    a.sflags[s] = (uint8_t)((pmag > (T)0 ? SFQ_ALIVE : 0) | SFQ_JUST_CREATED |
                                             ((m == 0 ? SFQ_ELECTRON : SFQ_POSITRON) << SFQ_SPECIES_SHIFT) |
                                             ((m + 1) << SFQ_TAG_SHIFT));
                     if (a.sfp[0]) {
@@ -241,7 +344,7 @@ __device__ __forceinline__ void process_events(const StepArgs<T> &a, const QEntr
             }
         }
         a.flags[e.i] = (uint8_t)(fl & ~SFQ_ALIVE);
-    } else {
+    } else if (nprod) {
         // photon emission: xi = s/(1+s) to the photon, the lepton keeps gamma/(1+s)
         const T s = xa;
         const T inv1s = (T)1 / ((T)1 + s);
@@ -257,7 +360,10 @@ __device__ __forceinline__ void process_events(const StepArgs<T> &a, const QEntr
             ++c.v[C_DROP];
         }
         a.px[e.i] = nx * pnew; a.py[e.i] = ny * pnew; a.pz[e.i] = nz * pnew;
-        a.tau[e.i] = to_tau<T>(fresh_tau(xb));                  // fresh optical depth, word 0 (Sec. 2)
+        if (xb > (T)0) a.tau[e.i] = to_tau<T>(fresh_tau(xb));   // fresh optical depth, word 0 (Sec. 2)
+        // a lepton left without momentum is outside the ultrarelativistic regime of the rates
+        // and has no direction for collinear emission: it leaves the step
+        if (!(pnew > (T)0)) a.flags[e.i] = (uint8_t)(fl & ~SFQ_ALIVE);
     }
 }
 
@@ -273,7 +379,7 @@ __global__ void __launch_bounds__(STEP_BS, SFQ_STEP_MINB) mc_step_kernel(const S
     using RS = RateSmem<T>;
     __shared__ __align__(16) T s_nlc[RS::NLC_N];
     __shared__ __align__(16) T s_nbw[RS::NBW_N];
-    __shared__ QEntry<T> wq[WARPS][QS];
+    __shared__ QEntryX<T> wq[WARPS][QS];
 
     stage_rate_table<T, Q::NLC_DEG, RS::NLC_STRIDE>(s_nlc, a.tab.nlc_rate, Q::RATE_NLC_N / (Q::NLC_DEG + 1),
                                                      threadIdx.x, STEP_BS);
@@ -282,12 +388,13 @@ __global__ void __launch_bounds__(STEP_BS, SFQ_STEP_MINB) mc_step_kernel(const S
     __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    QEntry<T> *q = wq[warp];
+    QEntryX<T> *q = wq[warp];
     unsigned head = 0, tail = 0;            // warp-uniform ring indices
     Cnt c;
     c.zero();
     constexpr int CH = 32 * PPT;
-    const int64_t nchunks = (a.n + CH - 1) / CH;
+    const int64_t n_eff = effective_n(a);
+    const int64_t nchunks = (n_eff + CH - 1) / CH;
     const int64_t gw = (int64_t)blockIdx.x * WARPS + warp, nw = (int64_t)gridDim.x * WARPS;
     for (int64_t ch = gw; ch < nchunks; ch += nw) {
         const int64_t base = ch * CH;
@@ -295,14 +402,19 @@ __global__ void __launch_bounds__(STEP_BS, SFQ_STEP_MINB) mc_step_kernel(const S
         for (int k = 0; k < PPT; ++k) {
             const int64_t i = base + k * 32 + lane;
             bool ev = false;
-            T g = (T)0, chi = (T)0;
-            if (i < a.n) {
+            T g = (T)0, chi = (T)0, aux = (T)-1;
+            if (i < n_eff) {
                 const uint8_t fl = a.flags[i];
-                if (fl & SFQ_ALIVE) {
+                const bool photon_f = ((fl >> SFQ_SPECIES_SHIFT) & 3) == SFQ_PHOTON;
+                if ((fl & SFQ_ALIVE) && !photon_f && a.lepton_model == SFQ_LEPTON_BLCFA_LOCAL) {
+                    T E[3], B[3];
+                    load_fields<T, FK>(a, i, E, B);
+                    ev = blcfa_phase_a<T>(a, s_nlc, i, fl, a.px[i], a.py[i], a.pz[i], E, B, g, chi, aux, c);
+                } else if (fl & SFQ_ALIVE) {
                     const T px = a.px[i], py = a.py[i], pz = a.pz[i];
                     T E[3], B[3];
                     load_fields<T, FK>(a, i, E, B);
-                    const bool photon = ((fl >> SFQ_SPECIES_SHIFT) & 3) == SFQ_PHOTON;
+                    const bool photon = photon_f;
                     const T p2 = fma(px, px, fma(py, py, pz * pz));
                     g = photon ? sqrt(p2) : sqrt((T)1 + p2);
                     chi = chi_of<T>(g, px, py, pz, E, B, a.inv_rho);
@@ -326,28 +438,29 @@ __global__ void __launch_bounds__(STEP_BS, SFQ_STEP_MINB) mc_step_kernel(const S
             const unsigned m = __ballot_sync(0xFFFFFFFFu, ev);
             if (ev) {
                 const unsigned r = __popc(m & ((1u << lane) - 1u));
-                QEntry<T> e;
+                QEntryX<T> e;
                 e.i = i;
                 e.g = g;
                 e.chi = chi;
+                e.aux = aux;
                 q[(tail + r) & (QS - 1)] = e;
             }
             tail += __popc(m);
         }
         __syncwarp();
         while (tail - head >= 32u) {
-            const QEntry<T> e = q[(head + lane) & (QS - 1)];
+            const QEntryX<T> e = q[(head + lane) & (QS - 1)];
             __syncwarp();
             head += 32;
-            process_events<T>(a, e, true, c);
+            process_events<T>(a, e, e.aux, true, c);
         }
     }
     // drain the partial batch
     __syncwarp();
     if (tail != head) {
         const unsigned nv = tail - head;
-        QEntry<T> e = q[(head + lane) & (QS - 1)];
-        process_events<T>(a, e, (unsigned)lane < nv, c);
+        QEntryX<T> e = q[(head + lane) & (QS - 1)];
+        process_events<T>(a, e, e.aux, (unsigned)lane < nv, c);
     }
     flush_counters(c, a.counters);
 }

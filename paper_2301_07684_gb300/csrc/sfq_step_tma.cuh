@@ -53,9 +53,9 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 }
 
 // Layout of one stage for TILE particles.
-template <typename T, int FK>
+template <typename T, int FK, int CW>
 struct TmaStage {
-    static constexpr int TILE = sizeof(T) == 4 ? 1024 : 512;
+    static constexpr int TILE = CW * (sizeof(T) == 4 ? 64 : 32);     // 2 (binary32) or 1 particle per lane
     static constexpr int NF = FK == FK_SOA ? 6 : 0;
     static constexpr size_t O_PX = 0, O_PY = O_PX + TILE * sizeof(T), O_PZ = O_PY + TILE * sizeof(T);
     static constexpr size_t O_TAU = O_PZ + TILE * sizeof(T);
@@ -66,9 +66,9 @@ struct TmaStage {
     static constexpr size_t BYTES = FK == FK_SOA ? O_F + NF * TILE * sizeof(T) : O_AMP + TILE * sizeof(T);
 };
 
-template <typename T, int FK>
+template <typename T, int FK, int CW>
 constexpr size_t tma_smem_bytes() {
-    return (size_t)TMA_NSTAGE * TmaStage<T, FK>::BYTES + 2 * TMA_NSTAGE * sizeof(uint64_t) + 64;
+    return (size_t)TMA_NSTAGE * TmaStage<T, FK, CW>::BYTES + 2 * TMA_NSTAGE * sizeof(uint64_t) + 64;
 }
 
 // Per-lane computation of the rate and the optical-depth test for one particle held
@@ -140,7 +140,7 @@ __device__ __forceinline__ void raise_timeout(sfq_counters *c) {
 template <typename T, int FK, int CW>
 __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const StepArgs<T> a) {
     using Q = L<T>;
-    using S = TmaStage<T, FK>;
+    using S = TmaStage<T, FK, CW>;
     constexpr int TMA_CONSUMER_WARPS = CW;
     constexpr int TMA_THREADS = 32 * (CW + 1);
     constexpr int TILE = S::TILE;
@@ -172,7 +172,8 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
     }
     __syncthreads();
 
-    const int64_t ntiles = (a.n + TILE - 1) / TILE;
+    const int64_t n_eff = effective_n(a);
+    const int64_t ntiles = (n_eff + TILE - 1) / TILE;
     const bool has_amp = a.amp != nullptr;
 
     if (warp == TMA_CONSUMER_WARPS) {
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
                 }
                 const int64_t start = tile * TILE;
                 unsigned char *st = smem + (size_t)s * S::BYTES;
-                if (start + TILE <= a.n) {
+                if (start + TILE <= n_eff) {
                     const uint32_t bytes = (uint32_t)(FK == FK_SOA ? S::BYTES
                                                                    : (has_amp ? S::BYTES : S::O_AMP));
                     mbar_arrive_tx(&full[s], bytes);
@@ -236,7 +237,7 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
             break;
         }
         const int64_t start = tile * TILE;
-        const bool staged = start + TILE <= a.n;
+        const bool staged = start + TILE <= n_eff;
         const unsigned char *st = smem + (size_t)s * S::BYTES;
         const T *spx = reinterpret_cast<const T *>(st + S::O_PX);
         const T *spy = reinterpret_cast<const T *>(st + S::O_PY);
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
                 ev[k] = false;
                 gk[k] = (T)0;
                 ck[k] = (T)0;
-                if (i < a.n) {
+                if (i < n_eff) {
                     const uint8_t fl = a.flags[i];
                     if (fl & SFQ_ALIVE) {
                         T E[3], B[3];
@@ -362,14 +363,14 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
             const QEntry<T> e = q[(head + lane) & (QS - 1)];
             __syncwarp();
             head += 32;
-            process_events<T>(a, e, true, c);
+            process_events<T>(a, e, (T)-1, true, c);
         }
     }
     __syncwarp();
     if (tail != head) {
         const unsigned nv = tail - head;
         QEntry<T> e = q[(head + lane) & (QS - 1)];
-        process_events<T>(a, e, (unsigned)lane < nv, c);
+        process_events<T>(a, e, (T)-1, (unsigned)lane < nv, c);
     }
     // counters of the consumer warps (the producer warp has returned)
     if (a.counters) {

@@ -56,6 +56,18 @@ def f_nlc_rate(chi):
     return Q.wtilde_rad(chi)
 
 
+def f_k23(x):
+    """x^{2/3} e^x K_2/3(x): bounded, -> 2^{-1/3} Gamma(2/3) as x -> 0."""
+    x = np.asarray(x, dtype=np.float64)
+    return x ** (2.0 / 3.0) * Q.besselk_scaled(2.0 / 3.0, x)
+
+
+def f_ki13(x):
+    """e^x Ki_1/3(x), Ki_1/3(x) = int_x^inf K_1/3: -> pi/sqrt(3) as x -> 0."""
+    x = np.asarray(x, dtype=np.float64)
+    return Q.besselk_int_scaled(1.0 / 3.0, x)
+
+
 def f_nbw_rate(chi):
     chi = np.asarray(chi, dtype=np.float64)
     return Q.wtilde_pair(chi) * np.exp(8.0 / (3.0 * chi)) / chi
@@ -161,6 +173,12 @@ def layouts():
     L["nlc_rate_f32"] = Table1D("nlc_rate_f32", FIT.Axis("octave", e_lo=-10, e_hi=20, sub=0, low=True, sub_low=0), 8, 5e-8)
     L["nbw_rate_f64"] = Table1D("nbw_rate_f64", FIT.Axis("octave", e_lo=-7, e_hi=20, sub=1, low=False), 10, 5e-12)
     L["nbw_rate_f32"] = Table1D("nbw_rate_f32", FIT.Axis("octave", e_lo=-7, e_hi=20, sub=0, low=False), 8, 5e-8)
+    # special functions of the spectrum Eq. pe_dp (beyond-LCFA rejection, Eq. rej_cond):
+    # x = 2u/(3 chi) in [2^-64, 2^12), octaves in x
+    L["k23_f64"] = Table1D("k23_f64", FIT.Axis("octave", e_lo=-64, e_hi=12, sub=1, low=False), 9, 5e-12)
+    L["k23_f32"] = Table1D("k23_f32", FIT.Axis("octave", e_lo=-64, e_hi=12, sub=0, low=False), 8, 5e-8)
+    L["ki13_f64"] = Table1D("ki13_f64", FIT.Axis("octave", e_lo=-64, e_hi=12, sub=1, low=False), 10, 5e-12)
+    L["ki13_f32"] = Table1D("ki13_f32", FIT.Axis("octave", e_lo=-64, e_hi=12, sub=0, low=False), 9, 5e-8)
     # inverses: chi up to 2^12 (the paper's domain ends at 2000)
     L["nlc_inv_f64"] = Table2D("nlc_inv_f64", FIT.Axis("octave", e_lo=-10, e_hi=12, sub=1, low=True, sub_low=0),
                                FIT.Axis("prob", e_lo=-6, sub=1, sub_low=0, q_lo=-24, sub_q=1), 11, 11, 5e-12)
@@ -230,6 +248,16 @@ def emit(tables, path=OUT, layout_path=OUT_LAYOUT):
         os.replace(tmp, pth)
 
 
+CACHE = os.path.join(os.path.dirname(os.path.dirname(HERE)), "_build", "fitgen_cache.npz")
+
+
+def _load_cache():
+    if os.path.exists(CACHE):
+        z = np.load(CACHE, allow_pickle=False)
+        return {k: z[k] for k in z.files}
+    return {}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--only", nargs="*", default=None)
@@ -238,19 +266,30 @@ def main(argv=None):
     args = ap.parse_args(argv)
     rng = np.random.default_rng(20230118)
     tables = layouts()
+    cache = _load_cache()
     for name, t in tables.items():
         if args.only and name not in args.only:
+            if name in cache:               # reuse a previous fit of the same layout
+                t.coef = cache[name]
+                t.err = float(cache[name + "__err"])
             continue
         t0 = time.time()
         if isinstance(t, Table1D):
-            fit_1d(t, f_nlc_rate if name.startswith("nlc") else f_nbw_rate, rng)
+            fn = {"nlc": f_nlc_rate, "nbw": f_nbw_rate, "k23": f_k23, "ki1": f_ki13}[name[:3]]
+            fit_1d(t, fn, rng)
         else:
             fit_2d(t, inv_nlc if name.startswith("nlc") else inv_nbw, rng, verbose=args.verbose)
         ok = "ok" if t.err <= t.target else "ABOVE TARGET"
         print(f"{name}: err {t.err:.3e} target {t.target:.1e} {ok} ({time.time() - t0:.1f}s)", flush=True)
-    if not args.only:
+        cache[name] = t.coef
+        cache[name + "__err"] = np.array(t.err)
+    os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+    np.savez(CACHE, **cache)
+    if all(t.coef is not None for t in tables.values()):
         emit(tables, args.out)
         print("wrote", args.out)
+    else:
+        print("not all tables fitted; nothing emitted")
 
 
 if __name__ == "__main__":

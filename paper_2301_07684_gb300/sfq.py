@@ -38,7 +38,7 @@ class Particles(C.Structure):
     _fields_ = [("n", C.c_int64), ("px", C.c_void_p), ("py", C.c_void_p), ("pz", C.c_void_p),
                 ("tau", C.c_void_p), ("id", C.c_void_p), ("id_base", C.c_uint64), ("flags", C.c_void_p),
                 ("fprev", C.c_void_p * 3), ("dfprev", C.c_void_p * 3), ("lepton_model", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("reserved", C.c_int32), ("n_dev", C.c_void_p)]
 
 
 class Fields(C.Structure):
@@ -219,11 +219,12 @@ class ParticleBuffers:
     """Structure-of-arrays particle state on the device."""
 
     def __init__(self, px, py, pz, tau, flags, ids=None, id_base=0, fprev=None, dfprev=None,
-                 lepton_model=SFQ_LEPTON_LCFA_OD):
+                 lepton_model=SFQ_LEPTON_LCFA_OD, n_dev=None):
         self.px, self.py, self.pz, self.tau, self.flags = px, py, pz, tau, flags
         self.ids, self.id_base = ids, id_base
         self.fprev, self.dfprev = fprev, dfprev
         self.lepton_model = lepton_model
+        self.n_dev = n_dev          # optional int64 device tensor holding the live count
         self.n = px.numel()
 
     def descriptor(self, n=None):
@@ -237,6 +238,7 @@ class ParticleBuffers:
             P.fprev[k] = _ptr(self.fprev[k]) if self.fprev is not None else None
             P.dfprev[k] = _ptr(self.dfprev[k]) if self.dfprev is not None else None
         P.lepton_model = self.lepton_model
+        P.n_dev = _ptr(self.n_dev)
         return P
 
 

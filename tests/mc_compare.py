@@ -13,7 +13,7 @@ def _rel(a, b):
     return np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64)) / np.maximum(np.abs(b), 1e-300)
 
 
-def compare_lineages(ids, orc, gpu_final, gpu_prod, tol, nsteps, step0=0):
+def compare_lineages(ids, orc, gpu_final, gpu_prod, tol, nsteps, step0=0, check_final=True):
     """ids: primary ids checked; orc: oracle.mc_run result for those ids (same order);
     gpu_final: dict with px, py, pz, tau, flags for the same ids;
     gpu_prod: dict of numpy arrays (px, py, pz, parent_id, step, meta) of records whose
@@ -38,10 +38,11 @@ def compare_lineages(ids, orc, gpu_final, gpu_prod, tol, nsteps, step0=0):
         summary["excluded_records"] += len(o_key.get(pid, [])) - len(ok)
 
         def okey(k):
-            return (int(op["step"][k]), int(op["member"][k]))
+            return (int(op["step"][k]), int(op["member"][k]), int(op["parent_tag"][k]))
 
         def gkey(k):
-            return (int(gpu_prod["step"][k]), int((gpu_prod["meta"][k] >> 2) & 3))
+            m = int(gpu_prod["meta"][k])
+            return (int(gpu_prod["step"][k]), (m >> 2) & 3, (m >> 4) & 3)
 
         ok.sort(key=okey)
         gk.sort(key=gkey)
@@ -55,7 +56,7 @@ def compare_lineages(ids, orc, gpu_final, gpu_prod, tol, nsteps, step0=0):
                 else:
                     assert _rel(gv, ov) < tol * 10, (pid, name, gv, ov)
         summary["records"] += len(ok)
-        if first_near[j] < 0:
+        if first_near[j] < 0 and check_final:
             # final state of the primary
             assert bool(gpu_final["flags"][j] & 1) == bool(orc["flags"][j] & 1), pid
             for c, name in enumerate(("px", "py", "pz")):

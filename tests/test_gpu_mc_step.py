@@ -91,7 +91,7 @@ def gpu_subset(P, out, ids):
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 @pytest.mark.parametrize("field_mode", ["soa", "pw"])
-@pytest.mark.parametrize("variant,ppt", [(1, 0), (2, 0), (2, 4)], ids=["warp", "tma16", "tma8"])
+@pytest.mark.parametrize("variant,ppt", [(1, 0), (2, 0), (2, 8), (2, 20)], ids=["warp", "tma16", "tma8", "tma20"])
 def test_config2_small(oracle, precision, field_mode, variant, ppt):
     """Both kernels (warp-streaming and TMA-staged, whose last tile is partial here)."""
     ctx = _ctx(precision)
