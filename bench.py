@@ -238,10 +238,76 @@ def run_ours(args):
         torch.cuda.empty_cache()
         return out_d
 
+    def batched_leg():
+        """Config 4: 64 beams of mixed species in one population, their pairs stepped as
+        children, `--batched-steps` steps recorded into one CUDA graph, launch shape from
+        the autotuner; products sorted afterwards (timed separately)."""
+        from paper_2301_07684_gb300 import batch
+        db = W.config4(seed=rank, scale=args.batched_scale)
+        nb = int(db["px"].size)
+        nsteps_b = args.batched_steps
+        ctx = sfq.Context(ref_len_m=W.REF_LEN, dt=W.DT, precision="fp32", seed=777, device=local)
+        cap = int(48 * nb) + 4096
+        while True:
+            b = batch.BatchRun(ctx, db, products_cap=cap)
+            b.P.id_base = rank * nb
+            variant, shape, tune_ms = b.autotune(sample_n=0)
+            init = [t.clone() for t in (b.P.px, b.P.py, b.P.pz, b.P.tau, b.P.flags)]
+
+            def reset():
+                for dst, src in zip((b.P.px, b.P.py, b.P.pz, b.P.tau, b.P.flags), init):
+                    dst.copy_(src)
+                b.spawn_count.zero_()
+                b.out.count.zero_()
+                b.counters.zero_()
+
+            reset()
+            b.run(0, nsteps_b)                     # records the graph (cached) and warms up
+            torch.cuda.synchronize()
+            c = sfq.counters_dict(b.counters)
+            if c["dropped"] == 0 and c["spawn_dropped"] == 0:
+                break
+            cap = int(1.1 * b.out.n()) + 4096      # grow the product buffer and record again
+            del b, init
+            torch.cuda.empty_cache()
+        reset()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clocks = ClockSampler(local)
+        clocks.start()
+        e0.record()
+        b.run(0, nsteps_b)
+        e1.record()
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1)
+        c = sfq.counters_dict(b.counters)
+        nrec = b.out.n()
+        scratch = torch.empty(sfq.sort_scratch_bytes(nrec), dtype=torch.uint8, device=device)
+        e0.record()
+        b.sort(scratch)
+        e1.record()
+        torch.cuda.synchronize()
+        sort_ms = e0.elapsed_time(e1)
+        out_b = {"workload": "64 beams, counts log-uniform in [1e3, 4e6], mixed e-/e+/photon, "
+                             "a0 U[10, 300], gamma0 log-U[200, 1e4], plane-wave fields",
+                 "particles": nb, "children": b.n_children(), "steps": nsteps_b,
+                 "value": c["updates"] / (ms * 1e-3), "unit": UNIT, "ms_graph": ms, "ms_per_step": ms / nsteps_b,
+                 "updates": c["updates"], "events": c["events"], "products": nrec,
+                 "shape": {"variant": ["auto", "warp-streaming", "tma-staged"][variant], "shape": shape,
+                           "tuned_ms_per_step": tune_ms},
+                 "sort_ms": sort_ms, "sort_records_per_s": nrec / max(sort_ms, 1e-9) * 1e3,
+                 "precision": "fp32-mixed", "graph": "one CUDA graph for all steps", "clocks": clk}
+        del b, init, scratch
+        ctx.close()
+        torch.cuda.empty_cache()
+        return out_b
+
     main = one_path("fp32", "soa", args.steps, args.warmup, with_e2e=True)
     pw = one_path("fp32", "pw", args.steps, args.warmup, with_e2e=False)
     f64_steps = max(2, args.steps // 10)
     f64 = one_path("fp64", "soa", f64_steps, max(3, min(args.warmup, 3)), with_e2e=False)
+    batched = batched_leg() if args.batched_steps > 0 else None
 
     # max over ranks of the headline time
     t = torch.tensor([main["ms_per_step"]], device=device)
@@ -275,6 +341,7 @@ def run_ours(args):
             "plane_wave_fields": {"value": pw["value"], "unit": UNIT, "ms_per_step": pw["ms_per_step"],
                                   "achieved_gbs": pw["achieved_gbs"], "frac": pw["frac"],
                                   "bytes_per_update": pw["bytes_per_update"]},
+            "batched": batched,
             "events_per_update": main["events_per_update"],
             "device": dev_name,
         }
@@ -344,6 +411,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_PARTICLES)
+    ap.add_argument("--batched-steps", type=int, default=500,
+                    help="steps of the 64-beam batched run in one CUDA graph (0 skips it)")
+    ap.add_argument("--batched-scale", type=float, default=1.0,
+                    help="scale of the 64-beam particle counts")
     ap.add_argument("--oracle-particles", type=int, default=512)
     ap.add_argument("--oracle-steps", type=int, default=50)
     ap.add_argument("--traffic-per-update", type=float, default=None,

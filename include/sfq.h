@@ -218,6 +218,31 @@ sfq_status sfq_mc_step(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f
                        const sfq_products *out, const sfq_spawn *spawn, sfq_counters *counters,
                        void *stream);
 
+/* `nsteps` consecutive steps step0 ... step0+nsteps-1, recorded once into a CUDA graph and
+ * replayed (the graph is cached in the context for the same arguments, so a repeated call
+ * costs one graph launch).  Each step runs `children` first (if not NULL: a population
+ * with its own field source, typically the sfq_spawn target of `p` with a device count)
+ * and then `p`; it is equivalent to calling sfq_mc_step in that order for every step.
+ * The call must not be made while `stream` is being captured. */
+sfq_status sfq_mc_run(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, const sfq_particles *children,
+                      const sfq_fields *children_fields, uint32_t step0, uint32_t nsteps, const sfq_products *out,
+                      const sfq_spawn *spawn, sfq_counters *counters, void *stream);
+
+/* Autotuner: times every launch shape of sfq_mc_step (kernel variant, particles per lane
+ * or warps per block) on a copy of up to `sample_n` particles of `p` (the caller's state
+ * is not modified; the copy lives in temporary device memory for the duration of the
+ * call), keeps the fastest in the context (sfq_set_step_shape) and returns it.  Products
+ * of the trial steps go to a temporary buffer.  Synchronises `stream`. */
+sfq_status sfq_autotune_step(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, uint32_t step,
+                             int64_t sample_n, int32_t *variant, int32_t *shape, double *ms_per_step, void *stream);
+
+/* Sort the first n product records in place by (parent id, step, member, parent tag)
+ * (a stable LSD radix sort).  `scratch` is caller-owned device memory of at least
+ * sfq_sort_scratch_bytes(n) bytes.  Returns SFQ_ERR_ARG if it is NULL or too small. */
+size_t sfq_sort_scratch_bytes(int64_t n);
+sfq_status sfq_sort_products(sfq_ctx *ctx, const sfq_products *out, int64_t n, void *scratch, size_t scratch_bytes,
+                             void *stream);
+
 /* Launch shape of sfq_mc_step for this context, the knob the autotuner turns.
  *   variant: 0 = automatic; 1 = warp-streaming kernel (each warp loads its particles
  *            directly); 2 = TMA-staged kernel (bulk copies of each tile into shared

@@ -55,6 +55,66 @@ bool is_fp64(const sfq_ctx *ctx) { return ctx->cfg.precision == SFQ_FP64; }
 
 }  // namespace
 
+namespace sfq {
+
+sfq_status validate_step(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, const sfq_products *out,
+                         const sfq_spawn *spawn, const sfq_counters *counters) {
+    if (!p || !f || !out) return fail(ctx, SFQ_ERR_ARG, "null descriptor");
+    if (p->n < 0 || out->capacity < 0) return fail(ctx, SFQ_ERR_ARG, "negative size");
+    if (p->lepton_model != SFQ_LEPTON_LCFA_OD && p->lepton_model != SFQ_LEPTON_BLCFA_LOCAL)
+        return fail(ctx, SFQ_ERR_ARG, "unknown lepton model");
+    if (p->n == 0) return SFQ_OK;
+    if (p->lepton_model == SFQ_LEPTON_BLCFA_LOCAL) {
+        for (int k = 0; k < 3; ++k)
+            if (!p->fprev[k] || !p->dfprev[k] || !aligned16(p->fprev[k]) || !aligned16(p->dfprev[k]))
+                return fail(ctx, SFQ_ERR_ARG, "beyond-LCFA state arrays null or misaligned");
+    }
+    if (p->n_dev && !aligned8(p->n_dev)) return fail(ctx, SFQ_ERR_ARG, "n_dev misaligned");
+    const void *need16[] = {p->px, p->py, p->pz, p->tau, p->flags};
+    for (const void *q : need16)
+        if (!q || !aligned16(q)) return fail(ctx, SFQ_ERR_ARG, "particle buffer null or misaligned");
+    if (p->id && !aligned16(p->id)) return fail(ctx, SFQ_ERR_ARG, "id misaligned");
+    if (f->kind == SFQ_FIELDS_SOA) {
+        const void *fl[] = {f->ex, f->ey, f->ez, f->bx, f->by, f->bz};
+        for (const void *q : fl)
+            if (!q || !aligned16(q)) return fail(ctx, SFQ_ERR_ARG, "field buffer null or misaligned");
+    } else if (f->kind == SFQ_FIELDS_PLANE_WAVE) {
+        if (!f->k0 || !f->table || f->n_table == 0 || !aligned16(f->k0) || !aligned16(f->table) ||
+            (f->amp && !aligned16(f->amp)))
+            return fail(ctx, SFQ_ERR_ARG, "plane-wave description null or misaligned");
+    } else {
+        return fail(ctx, SFQ_ERR_ARG, "unknown field kind");
+    }
+    if (!out->count || !aligned8(out->count)) return fail(ctx, SFQ_ERR_ARG, "product counter null or misaligned");
+    if (out->capacity > 0) {
+        const void *ob[] = {out->px, out->py, out->pz, out->parent_id, out->step, out->meta};
+        for (const void *q : ob)
+            if (!q || !aligned16(q)) return fail(ctx, SFQ_ERR_ARG, "product buffer null or misaligned");
+    }
+    if (spawn) {
+        if (!spawn->count || spawn->p.n < 0) return fail(ctx, SFQ_ERR_ARG, "spawn counter null or negative capacity");
+        if (spawn->p.n > 0) {
+            const void *sb[] = {spawn->p.px, spawn->p.py, spawn->p.pz, spawn->p.tau, spawn->p.id, spawn->p.flags};
+            for (const void *q : sb)
+                if (!q || !aligned16(q)) return fail(ctx, SFQ_ERR_ARG, "spawn buffer null or misaligned");
+            if (f->kind == SFQ_FIELDS_PLANE_WAVE && !spawn->k0)
+                return fail(ctx, SFQ_ERR_ARG, "spawn needs k0 for plane-wave fields");
+        }
+    }
+    if (counters && !aligned8(counters)) return fail(ctx, SFQ_ERR_ARG, "counters misaligned");
+    return SFQ_OK;
+}
+
+cudaError_t launch_step(const sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, uint32_t step,
+                        const sfq_products *out, const sfq_spawn *spawn, sfq_counters *counters, cudaStream_t stream) {
+    if (p->n == 0) return cudaSuccess;
+    const int ppt = ctx->step_ppt ? ctx->step_ppt : (ctx->cfg.precision == SFQ_FP64 ? 1 : 2);
+    StepLaunch L{ctx, p, f, step, out, spawn, counters, stream, ctx->step_grid, ppt, ctx->step_variant};
+    return ctx->cfg.precision == SFQ_FP64 ? launch_step_f64(L) : launch_step_f32(L);
+}
+
+}  // namespace sfq
+
 extern "C" {
 
 const char *sfq_version(void) { return "libsfq 0.1 (sm_103a)"; }
@@ -104,6 +164,7 @@ void sfq_finalize(sfq_ctx *ctx) {
     if (!ctx) return;
     {
         DeviceGuard g(ctx->device);
+        sfq::release_graphs(ctx);
         void *ptrs[6] = {ctx->d_nlc_rate, ctx->d_nbw_rate, ctx->d_nlc_inv, ctx->d_nbw_inv, ctx->d_k23, ctx->d_ki13};
         for (void *p : ptrs)
             if (p) cudaFree(p);
@@ -189,54 +250,11 @@ sfq_status sfq_sample_pair_xi(sfq_ctx *ctx, int64_t n, const void *chi, const vo
 sfq_status sfq_mc_step(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, uint32_t step,
                        const sfq_products *out, const sfq_spawn *spawn, sfq_counters *counters, void *stream) {
     if (!ctx) return SFQ_ERR_ARG;
-    if (!p || !f || !out) return fail(ctx, SFQ_ERR_ARG, "null descriptor");
-    if (p->n < 0 || out->capacity < 0) return fail(ctx, SFQ_ERR_ARG, "negative size");
-    if (p->lepton_model != SFQ_LEPTON_LCFA_OD && p->lepton_model != SFQ_LEPTON_BLCFA_LOCAL)
-        return fail(ctx, SFQ_ERR_ARG, "unknown lepton model");
-    if (p->lepton_model == SFQ_LEPTON_BLCFA_LOCAL && p->n > 0) {
-        for (int k = 0; k < 3; ++k)
-            if (!p->fprev[k] || !p->dfprev[k] || !aligned16(p->fprev[k]) || !aligned16(p->dfprev[k]))
-                return fail(ctx, SFQ_ERR_ARG, "beyond-LCFA state arrays null or misaligned");
-    }
-    if (p->n_dev && !aligned8(p->n_dev)) return fail(ctx, SFQ_ERR_ARG, "n_dev misaligned");
+    const sfq_status st = sfq::validate_step(ctx, p, f, out, spawn, counters);
+    if (st != SFQ_OK) return st;
     if (p->n == 0) return SFQ_OK;
-    const void *need16[] = {p->px, p->py, p->pz, p->tau, p->flags};
-    for (const void *q : need16)
-        if (!q || !aligned16(q)) return fail(ctx, SFQ_ERR_ARG, "particle buffer null or misaligned");
-    if (p->id && !aligned16(p->id)) return fail(ctx, SFQ_ERR_ARG, "id misaligned");
-    if (f->kind == SFQ_FIELDS_SOA) {
-        const void *fl[] = {f->ex, f->ey, f->ez, f->bx, f->by, f->bz};
-        for (const void *q : fl)
-            if (!q || !aligned16(q)) return fail(ctx, SFQ_ERR_ARG, "field buffer null or misaligned");
-    } else if (f->kind == SFQ_FIELDS_PLANE_WAVE) {
-        if (!f->k0 || !f->table || f->n_table == 0 || !aligned16(f->k0) || !aligned16(f->table) ||
-            (f->amp && !aligned16(f->amp)))
-            return fail(ctx, SFQ_ERR_ARG, "plane-wave description null or misaligned");
-    } else {
-        return fail(ctx, SFQ_ERR_ARG, "unknown field kind");
-    }
-    if (!out->count || !aligned8(out->count)) return fail(ctx, SFQ_ERR_ARG, "product counter null or misaligned");
-    if (out->capacity > 0) {
-        const void *ob[] = {out->px, out->py, out->pz, out->parent_id, out->step, out->meta};
-        for (const void *q : ob)
-            if (!q || !aligned16(q)) return fail(ctx, SFQ_ERR_ARG, "product buffer null or misaligned");
-    }
-    if (spawn) {
-        if (!spawn->count || spawn->p.n < 0) return fail(ctx, SFQ_ERR_ARG, "spawn counter null or negative capacity");
-        if (spawn->p.n > 0) {
-            const void *sb[] = {spawn->p.px, spawn->p.py, spawn->p.pz, spawn->p.tau, spawn->p.id, spawn->p.flags};
-            for (const void *q : sb)
-                if (!q || !aligned16(q)) return fail(ctx, SFQ_ERR_ARG, "spawn buffer null or misaligned");
-            if (f->kind == SFQ_FIELDS_PLANE_WAVE && !spawn->k0)
-                return fail(ctx, SFQ_ERR_ARG, "spawn needs k0 for plane-wave fields");
-        }
-    }
-    if (counters && !aligned8(counters)) return fail(ctx, SFQ_ERR_ARG, "counters misaligned");
     DeviceGuard g(ctx->device);
-    const int ppt = ctx->step_ppt ? ctx->step_ppt : (is_fp64(ctx) ? 1 : 2);
-    sfq::StepLaunch L{ctx, p, f, step, out, spawn, counters, (cudaStream_t)stream, ctx->step_grid, ppt,
-                      ctx->step_variant};
-    const cudaError_t e = is_fp64(ctx) ? sfq::launch_step_f64(L) : sfq::launch_step_f32(L);
+    const cudaError_t e = sfq::launch_step(ctx, p, f, step, out, spawn, counters, (cudaStream_t)stream);
     return e == cudaSuccess ? SFQ_OK : cuda_fail(ctx, e, "sfq_mc_step");
 }
 

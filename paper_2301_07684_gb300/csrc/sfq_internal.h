@@ -2,6 +2,8 @@
 #pragma once
 #include <cstdint>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -15,6 +17,7 @@ struct sfq_ctx {
     void *d_nlc_rate, *d_nbw_rate, *d_nlc_inv, *d_nbw_inv, *d_k23, *d_ki13;
     int num_sms;
     int step_variant = 0;    // 0 = automatic, 1 = warp-streaming, 2 = TMA-staged
+    std::vector<std::pair<std::string, cudaGraphExec_t>> graphs;   // sfq_mc_run cache
     int step_ppt = 0;        // 0 = default
     int step_grid = 0;       // 0 = one wave of resident blocks
     std::string err;
@@ -66,6 +69,18 @@ cudaError_t launch_uniforms_f64(int64_t n, const uint64_t *id, uint32_t step, ui
                                 void *u, cudaStream_t s, int grid);
 cudaError_t launch_step_f32(const StepLaunch &);
 cudaError_t launch_step_f64(const StepLaunch &);
+
+sfq_status validate_step(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, const sfq_products *out,
+                         const sfq_spawn *spawn, const sfq_counters *counters);
+cudaError_t launch_step(const sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, uint32_t step,
+                        const sfq_products *out, const sfq_spawn *spawn, sfq_counters *counters, cudaStream_t stream);
+// Dynamic shared-memory attributes of every kernel shape (before graph capture).
+cudaError_t prepare_step_f32();
+cudaError_t prepare_step_f64();
+cudaError_t sort_products(const sfq_products &out, int64_t n, size_t elem, void *scratch, cudaStream_t s,
+                          int num_sms);
+size_t sort_scratch_bytes(int64_t n, size_t elem);
+void release_graphs(sfq_ctx *ctx);
 
 // Host copies of the tables (sfq_tables_host.cu).
 struct HostTables {

@@ -52,6 +52,28 @@ static cudaError_t launch_uniforms_t(int64_t n, const uint64_t *id, uint32_t ste
     return cudaGetLastError();
 }
 
+// Dynamic shared-memory limits of the TMA-staged kernels, set once per process (and before
+// any stream capture, where the launch itself is recorded).
+template <typename T>
+static cudaError_t prepare_step_t() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+#define SFQ_PREP(CWV)                                                                                         \
+    if (e == cudaSuccess)                                                                                     \
+        e = cudaFuncSetAttribute(mc_step_tma_kernel<T, FK_SOA, CWV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)tma_smem_bytes<T, FK_SOA, CWV>());                                     \
+    if (e == cudaSuccess)                                                                                     \
+        e = cudaFuncSetAttribute(mc_step_tma_kernel<T, FK_PW, CWV>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                 (int)tma_smem_bytes<T, FK_PW, CWV>());
+    SFQ_PREP(8)
+    SFQ_PREP(16)
+    SFQ_PREP(20)
+#undef SFQ_PREP
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
 template <typename T>
 static cudaError_t launch_step_t(const StepLaunch &L) {
     const sfq_particles &p = *L.p;
@@ -134,8 +156,9 @@ static cudaError_t launch_step_t(const StepLaunch &L) {
             SFQ_TMA_CASE(16)
         }
 #undef SFQ_TMA_CASE
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = prepare_step_t<T>();
         if (e != cudaSuccess) return e;
+        (void)smem;
         const int64_t ntiles = (p.n + tile - 1) / tile;
         int grid = L.grid > 0 ? L.grid : ctx->num_sms;
         if (ntiles < grid) grid = (int)ntiles;

@@ -9,4 +9,5 @@ cudaError_t launch_uniforms_f32(int64_t n, const uint64_t *id, uint32_t step, ui
     return launch_uniforms_t<float>(n, id, step, tag, seed, u, s, grid);
 }
 cudaError_t launch_step_f32(const StepLaunch &L) { return launch_step_t<float>(L); }
+cudaError_t prepare_step_f32() { return prepare_step_t<float>(); }
 }  // namespace sfq

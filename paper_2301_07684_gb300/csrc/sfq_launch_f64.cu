@@ -9,4 +9,5 @@ cudaError_t launch_uniforms_f64(int64_t n, const uint64_t *id, uint32_t step, ui
     return launch_uniforms_t<double>(n, id, step, tag, seed, u, s, grid);
 }
 cudaError_t launch_step_f64(const StepLaunch &L) { return launch_step_t<double>(L); }
+cudaError_t prepare_step_f64() { return prepare_step_t<double>(); }
 }  // namespace sfq

@@ -367,6 +367,68 @@ __device__ __forceinline__ void process_events(const StepArgs<T> &a, const E &e,
     }
 }
 
+// Per-lane computation of the rate and the optical-depth test for one particle held
+// in registers; returns true on an event (tau is then left to the event path).  Every
+// kernel shape calls this one routine, so results do not depend on the launch shape.
+template <typename T>
+__device__ __forceinline__ bool step_particle(const StepArgs<T> &a, const T *s_nlc, const T *s_nbw, int64_t i,
+                                              uint8_t fl, T px, T py, T pz, const T E[3], const T B[3],
+                                              double tau_in, T &g, T &chi, Cnt &c) {
+    const bool photon = ((fl >> SFQ_SPECIES_SHIFT) & 3) == SFQ_PHOTON;
+    const T p2 = fma(px, px, fma(py, py, pz * pz));
+    // gamma and 1/gamma from one reciprocal square root
+    const T g2 = photon ? p2 : (T)1 + p2;
+    const T inv_g = g2 > (T)0 ? rsqrt_nr(g2) : (T)0;
+    g = sqrt_nr(g2);
+    chi = chi_of<T>(g, px, py, pz, E, B, a.inv_rho);
+    ++c.v[C_UPD];
+    bool oor = false;
+    T d;
+    if (!(chi >= (T)0) || !(g > (T)0)) {
+        ++c.v[C_NAN];
+        d = (T)0;
+    } else if (photon) {
+        d = a.prefdt * wtilde_pair<T>(s_nbw, chi, oor) * inv_g;
+    } else {
+        d = a.prefdt * (chi * inv_g) * wtilde_rad<T>(s_nlc, chi, oor);
+    }
+    c.v[C_OOR] += oor;
+    c.v[C_RDT] += d > (T)0.1;
+    const auto id_of = [&]() { return a.id ? a.id[i] : a.id_base + (uint64_t)i; };
+    double tau_v = tau_in;
+    const bool ev = od_update(&tau_v, d, a.seed, id_of, a.step, (fl >> SFQ_TAG_SHIFT) & 3u);
+    if (!ev) a.tau[i] = tau_v;
+    return ev;
+}
+
+// As step_particle, with the optical depth passed in and out (stored by the caller).
+template <typename T>
+__device__ __forceinline__ bool step_particle_v(const StepArgs<T> &a, const T *s_nlc, const T *s_nbw, int64_t i,
+                                                uint8_t fl, T px, T py, T pz, const T E[3], const T B[3],
+                                                double &tau, T &g, T &chi, Cnt &c) {
+    const bool photon = ((fl >> SFQ_SPECIES_SHIFT) & 3) == SFQ_PHOTON;
+    const T p2 = fma(px, px, fma(py, py, pz * pz));
+    const T g2 = photon ? p2 : (T)1 + p2;
+    const T inv_g = g2 > (T)0 ? rsqrt_nr(g2) : (T)0;
+    g = sqrt_nr(g2);
+    chi = chi_of<T>(g, px, py, pz, E, B, a.inv_rho);
+    ++c.v[C_UPD];
+    bool oor = false;
+    T d;
+    if (!(chi >= (T)0) || !(g > (T)0)) {
+        ++c.v[C_NAN];
+        d = (T)0;
+    } else if (photon) {
+        d = a.prefdt * wtilde_pair<T>(s_nbw, chi, oor) * inv_g;
+    } else {
+        d = a.prefdt * (chi * inv_g) * wtilde_rad<T>(s_nlc, chi, oor);
+    }
+    c.v[C_OOR] += oor;
+    c.v[C_RDT] += d > (T)0.1;
+    const auto id_of = [&]() { return a.id ? a.id[i] : a.id_base + (uint64_t)i; };
+    return od_update(&tau, d, a.seed, id_of, a.step, (fl >> SFQ_TAG_SHIFT) & 3u);
+}
+
 // T: float (mixed) or double; FK: field source; PPT: particles per lane per chunk.
 // Each warp streams chunks of 32*PPT particles and compacts event lanes into a
 // warp-private ring in shared memory; a full batch of 32 events is sampled by the
@@ -411,28 +473,10 @@ __global__ void __launch_bounds__(STEP_BS, SFQ_STEP_MINB) mc_step_kernel(const S
                     load_fields<T, FK>(a, i, E, B);
                     ev = blcfa_phase_a<T>(a, s_nlc, i, fl, a.px[i], a.py[i], a.pz[i], E, B, g, chi, aux, c);
                 } else if (fl & SFQ_ALIVE) {
-                    const T px = a.px[i], py = a.py[i], pz = a.pz[i];
                     T E[3], B[3];
                     load_fields<T, FK>(a, i, E, B);
-                    const bool photon = photon_f;
-                    const T p2 = fma(px, px, fma(py, py, pz * pz));
-                    g = photon ? sqrt(p2) : sqrt((T)1 + p2);
-                    chi = chi_of<T>(g, px, py, pz, E, B, a.inv_rho);
-                    ++c.v[C_UPD];
-                    bool oor = false;
-                    T d;
-                    if (!(chi >= (T)0) || !(g > (T)0)) {
-                        ++c.v[C_NAN];
-                        d = (T)0;
-                    } else if (photon) {
-                        d = a.prefdt * wtilde_pair<T>(s_nbw, chi, oor) / g;
-                    } else {
-                        d = a.prefdt * (chi / g) * wtilde_rad<T>(s_nlc, chi, oor);
-                    }
-                    c.v[C_OOR] += oor;
-                    c.v[C_RDT] += d > (T)0.1;
-                    const auto id_of = [&]() { return a.id ? a.id[i] : a.id_base + (uint64_t)i; };
-                    ev = od_update(a.tau + i, d, a.seed, id_of, a.step, (fl >> SFQ_TAG_SHIFT) & 3u);
+                    ev = step_particle<T>(a, s_nlc, s_nbw, i, fl, a.px[i], a.py[i], a.pz[i], E, B, a.tau[i], g, chi,
+                                          c);
                 }
             }
             const unsigned m = __ballot_sync(0xFFFFFFFFu, ev);

@@ -71,67 +71,6 @@ constexpr size_t tma_smem_bytes() {
     return (size_t)TMA_NSTAGE * TmaStage<T, FK, CW>::BYTES + 2 * TMA_NSTAGE * sizeof(uint64_t) + 64;
 }
 
-// Per-lane computation of the rate and the optical-depth test for one particle held
-// in registers; returns true on an event (tau is then left to the event path).
-template <typename T>
-__device__ __forceinline__ bool step_particle(const StepArgs<T> &a, const T *s_nlc, const T *s_nbw, int64_t i,
-                                              uint8_t fl, T px, T py, T pz, const T E[3], const T B[3],
-                                              double tau_in, T &g, T &chi, Cnt &c) {
-    const bool photon = ((fl >> SFQ_SPECIES_SHIFT) & 3) == SFQ_PHOTON;
-    const T p2 = fma(px, px, fma(py, py, pz * pz));
-    // gamma and 1/gamma from one reciprocal square root
-    const T g2 = photon ? p2 : (T)1 + p2;
-    const T inv_g = g2 > (T)0 ? rsqrt_nr(g2) : (T)0;
-    g = sqrt_nr(g2);
-    chi = chi_of<T>(g, px, py, pz, E, B, a.inv_rho);
-    ++c.v[C_UPD];
-    bool oor = false;
-    T d;
-    if (!(chi >= (T)0) || !(g > (T)0)) {
-        ++c.v[C_NAN];
-        d = (T)0;
-    } else if (photon) {
-        d = a.prefdt * wtilde_pair<T>(s_nbw, chi, oor) * inv_g;
-    } else {
-        d = a.prefdt * (chi * inv_g) * wtilde_rad<T>(s_nlc, chi, oor);
-    }
-    c.v[C_OOR] += oor;
-    c.v[C_RDT] += d > (T)0.1;
-    const auto id_of = [&]() { return a.id ? a.id[i] : a.id_base + (uint64_t)i; };
-    double tau_v = tau_in;
-    const bool ev = od_update(&tau_v, d, a.seed, id_of, a.step, (fl >> SFQ_TAG_SHIFT) & 3u);
-    if (!ev) a.tau[i] = tau_v;
-    return ev;
-}
-
-// As step_particle, with the optical depth passed in and out (stored by the caller).
-template <typename T>
-__device__ __forceinline__ bool step_particle_v(const StepArgs<T> &a, const T *s_nlc, const T *s_nbw, int64_t i,
-                                                uint8_t fl, T px, T py, T pz, const T E[3], const T B[3],
-                                                double &tau, T &g, T &chi, Cnt &c) {
-    const bool photon = ((fl >> SFQ_SPECIES_SHIFT) & 3) == SFQ_PHOTON;
-    const T p2 = fma(px, px, fma(py, py, pz * pz));
-    const T g2 = photon ? p2 : (T)1 + p2;
-    const T inv_g = g2 > (T)0 ? rsqrt_nr(g2) : (T)0;
-    g = sqrt_nr(g2);
-    chi = chi_of<T>(g, px, py, pz, E, B, a.inv_rho);
-    ++c.v[C_UPD];
-    bool oor = false;
-    T d;
-    if (!(chi >= (T)0) || !(g > (T)0)) {
-        ++c.v[C_NAN];
-        d = (T)0;
-    } else if (photon) {
-        d = a.prefdt * wtilde_pair<T>(s_nbw, chi, oor) * inv_g;
-    } else {
-        d = a.prefdt * (chi * inv_g) * wtilde_rad<T>(s_nlc, chi, oor);
-    }
-    c.v[C_OOR] += oor;
-    c.v[C_RDT] += d > (T)0.1;
-    const auto id_of = [&]() { return a.id ? a.id[i] : a.id_base + (uint64_t)i; };
-    return od_update(&tau, d, a.seed, id_of, a.step, (fl >> SFQ_TAG_SHIFT) & 3u);
-}
-
 // A wait that gave up is recorded in the counters.
 __device__ __forceinline__ void raise_timeout(sfq_counters *c) {
     if (c) atomicAdd(&c->timeouts, 1ull);

@@ -86,6 +86,16 @@ def lib():
         L.sfq_mc_step.argtypes = [vp, C.POINTER(Particles), C.POINTER(Fields), u32, C.POINTER(Products),
                                   C.POINTER(Spawn), vp, vp]
         L.sfq_mc_step.restype = st
+        L.sfq_mc_run.argtypes = [vp, C.POINTER(Particles), C.POINTER(Fields), C.POINTER(Particles),
+                                 C.POINTER(Fields), u32, u32, C.POINTER(Products), C.POINTER(Spawn), vp, vp]
+        L.sfq_mc_run.restype = st
+        L.sfq_autotune_step.argtypes = [vp, C.POINTER(Particles), C.POINTER(Fields), u32, i64,
+                                        C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_double), vp]
+        L.sfq_autotune_step.restype = st
+        L.sfq_sort_scratch_bytes.argtypes = [i64]
+        L.sfq_sort_scratch_bytes.restype = C.c_size_t
+        L.sfq_sort_products.argtypes = [vp, C.POINTER(Products), i64, vp, C.c_size_t, vp]
+        L.sfq_sort_products.restype = st
         L.sfq_set_step_shape.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
         L.sfq_set_step_shape.restype = st
         L.sfq_version.restype = C.c_char_p
@@ -94,7 +104,8 @@ def lib():
 
 
 EXPORTED = ["sfq_init", "sfq_finalize", "sfq_last_error", "sfq_constants", "sfq_photon_rate", "sfq_pair_rate",
-            "sfq_uniforms", "sfq_sample_photon_xi", "sfq_sample_pair_xi", "sfq_mc_step", "sfq_set_step_shape",
+            "sfq_uniforms", "sfq_sample_photon_xi", "sfq_sample_pair_xi", "sfq_mc_step", "sfq_mc_run",
+            "sfq_autotune_step", "sfq_sort_scratch_bytes", "sfq_sort_products", "sfq_set_step_shape",
             "sfq_version"]
 
 
@@ -212,6 +223,40 @@ class Context:
         self._check(lib().sfq_mc_step(self._h, C.byref(P), C.byref(F), step, C.byref(O),
                                       C.byref(S) if S is not None else None, _ptr(counters), _stream()),
                     "sfq_mc_step")
+
+    def mc_run(self, particles: "ParticleBuffers", fields: "FieldSource", step0: int, nsteps: int,
+               products: "ProductBuffers", children: "ParticleBuffers" = None, children_fields: "FieldSource" = None,
+               spawn: "SpawnBuffers" = None, counters=None):
+        """nsteps steps in one CUDA graph (children first, then `particles`, every step)."""
+        P, F, O = particles.descriptor(), fields.descriptor(), products.descriptor()
+        Cp = children.descriptor() if children is not None else None
+        Cf = children_fields.descriptor() if children_fields is not None else None
+        S = spawn.descriptor() if spawn is not None else None
+        ref = lambda x: C.byref(x) if x is not None else None
+        self._check(lib().sfq_mc_run(self._h, C.byref(P), C.byref(F), ref(Cp), ref(Cf), step0, nsteps, C.byref(O),
+                                     ref(S), _ptr(counters), _stream()), "sfq_mc_run")
+
+    def autotune_step(self, particles: "ParticleBuffers", fields: "FieldSource", step=0, sample_n=0):
+        """Times every launch shape on a copy of the population; returns (variant, shape, ms)."""
+        P, F = particles.descriptor(), fields.descriptor()
+        v, sh, ms = C.c_int32(0), C.c_int32(0), C.c_double(0.0)
+        self._check(lib().sfq_autotune_step(self._h, C.byref(P), C.byref(F), step, sample_n, C.byref(v),
+                                            C.byref(sh), C.byref(ms), _stream()), "sfq_autotune_step")
+        return v.value, sh.value, ms.value
+
+    def sort_products(self, products: "ProductBuffers", n=None, scratch=None):
+        """Sorts the first n records by (parent id, step, member, parent tag) in place."""
+        n = min(products.n(), products.capacity) if n is None else n
+        need = sort_scratch_bytes(n)
+        if scratch is None:
+            scratch = torch.empty(need, dtype=torch.uint8, device=products.px.device)
+        O = products.descriptor()
+        self._check(lib().sfq_sort_products(self._h, C.byref(O), n, _ptr(scratch), scratch.numel(), _stream()),
+                    "sfq_sort_products")
+
+
+def sort_scratch_bytes(n):
+    return int(lib().sfq_sort_scratch_bytes(n))
 
 
 # --- buffers -------------------------------------------------------------------
