@@ -238,7 +238,10 @@ sfq_status sfq_autotune_step(sfq_ctx *ctx, const sfq_particles *p, const sfq_fie
 
 /* Sort the first n product records in place by (parent id, step, member, parent tag)
  * (a stable LSD radix sort).  `scratch` is caller-owned device memory of at least
- * sfq_sort_scratch_bytes(n) bytes.  Returns SFQ_ERR_ARG if it is NULL or too small. */
+ * sfq_sort_scratch_bytes(n) bytes, 256-byte aligned; nothing in it needs to start at zero.
+ * Synchronises `stream` once (to learn which key bits occur, so that passes over
+ * all-zero digits are skipped).  Returns SFQ_ERR_ARG if scratch is NULL, misaligned or
+ * too small, or if n exceeds the capacity of `out` or 2^32 - 1. */
 size_t sfq_sort_scratch_bytes(int64_t n);
 sfq_status sfq_sort_products(sfq_ctx *ctx, const sfq_products *out, int64_t n, void *scratch, size_t scratch_bytes,
                              void *stream);
