@@ -246,6 +246,23 @@ size_t sfq_sort_scratch_bytes(int64_t n);
 sfq_status sfq_sort_products(sfq_ctx *ctx, const sfq_products *out, int64_t n, void *scratch, size_t scratch_bytes,
                              void *stream);
 
+/* sfq_sort_products without caller scratch and without allocating (the paper has no
+ * counterpart: this is a runtime service).  The scratch is a fixed array of
+ * SFQ_SORT_NOALLOC_SCRATCH_BYTES in the library's own device memory, for callers that
+ * cannot allocate at the point of the call: host codes that give all device memory to
+ * their own pool at start-up and have no spare buffer, and step loops where a
+ * cudaMalloc/cudaFree would synchronise the device.
+ *   n: at most SFQ_SORT_NOALLOC_MAX_N records, else SFQ_ERR_ARG (use sfq_sort_products).
+ *   Nothing in the scratch needs to start at zero.
+ *   The array is shared by all calls on a device: calls that overlap in time on one
+ *   device race, so issue them on one stream or order their streams.
+ *   The first call on each device looks up the array's address (cudaGetSymbolAddress);
+ *   make that first call before any stream capture begins.
+ *   Synchronises `stream` once, as sfq_sort_products does. */
+#define SFQ_SORT_NOALLOC_MAX_N (1 << 20)
+#define SFQ_SORT_NOALLOC_SCRATCH_BYTES (44u << 20)
+sfq_status sfq_sort_products_noalloc(sfq_ctx *ctx, const sfq_products *out, int64_t n, void *stream);
+
 /* Launch shape of sfq_mc_step for this context, the knob the autotuner turns.
  *   variant: 0 = automatic; 1 = warp-streaming kernel (each warp loads its particles
  *            directly); 2 = TMA-staged kernel (bulk copies of each tile into shared

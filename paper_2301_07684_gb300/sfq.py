@@ -96,6 +96,8 @@ def lib():
         L.sfq_sort_scratch_bytes.restype = C.c_size_t
         L.sfq_sort_products.argtypes = [vp, C.POINTER(Products), i64, vp, C.c_size_t, vp]
         L.sfq_sort_products.restype = st
+        L.sfq_sort_products_noalloc.argtypes = [vp, C.POINTER(Products), i64, vp]
+        L.sfq_sort_products_noalloc.restype = st
         L.sfq_set_step_shape.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
         L.sfq_set_step_shape.restype = st
         L.sfq_version.restype = C.c_char_p
@@ -105,7 +107,7 @@ def lib():
 
 EXPORTED = ["sfq_init", "sfq_finalize", "sfq_last_error", "sfq_constants", "sfq_photon_rate", "sfq_pair_rate",
             "sfq_uniforms", "sfq_sample_photon_xi", "sfq_sample_pair_xi", "sfq_mc_step", "sfq_mc_run",
-            "sfq_autotune_step", "sfq_sort_scratch_bytes", "sfq_sort_products", "sfq_set_step_shape",
+            "sfq_autotune_step", "sfq_sort_scratch_bytes", "sfq_sort_products", "sfq_sort_products_noalloc", "sfq_set_step_shape",
             "sfq_version"]
 
 
@@ -253,6 +255,17 @@ class Context:
         O = products.descriptor()
         self._check(lib().sfq_sort_products(self._h, C.byref(O), n, _ptr(scratch), scratch.numel(), _stream()),
                     "sfq_sort_products")
+
+    def sort_products_noalloc(self, products: "ProductBuffers", n=None):
+        """As sort_products, with the library's fixed scratch (n <= SORT_NOALLOC_MAX_N)."""
+        n = min(products.n(), products.capacity) if n is None else n
+        O = products.descriptor()
+        self._check(lib().sfq_sort_products_noalloc(self._h, C.byref(O), n, _stream()),
+                    "sfq_sort_products_noalloc")
+
+
+SORT_NOALLOC_MAX_N = 1 << 20
+SORT_NOALLOC_SCRATCH_BYTES = 44 << 20
 
 
 def sort_scratch_bytes(n):
