@@ -192,6 +192,8 @@ def run_ours(args):
             k0 = torch.as_tensor(d["k0"].view(np.int32)).to(device)
             F = sfq.FieldSource.plane_wave(k0, table, d["k_step"], amp0=d["amp0"])
             fs = lambda s: F
+        # launch shape from the autotuner (timed on a copy of the population)
+        tuned = ctx.autotune_step(P, fs(0), 0)
         clocks = ClockSampler(local)
         clocks.start()
         total_ms, launch_ms = time_mc(sfq, torch, ctx, P, fs, steps, warmup, out, cnt, n)
@@ -232,7 +234,8 @@ def run_ours(args):
         out_d = dict(value=ups, ms_per_step=total_ms / steps, launch_ms=statistics.mean(launch_ms),
                      achieved_gbs=achieved, frac=achieved / hbm_peak, bytes_per_update=bytes_per_launch / n,
                      events_per_update=events_per_step / n, counters=c, clocks=clk, e2e=e2e,
-                     steps=steps)
+                     steps=steps, shape={"variant": ["auto", "warp-streaming", "tma-staged"][tuned[0]],
+                                         "shape": tuned[1]})
         slabs = None
         ctx.close()
         torch.cuda.empty_cache()
@@ -325,10 +328,13 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32 (f64 optical depth)", "data": "synthetic",
             "config": {"workload": WORKLOAD, "particles": n, "fields": "SoA, distinct slab per step",
                        "precision": "fp32-mixed", "l2": "inputs larger than L2 (~760 MB read per step)",
+                       "launch_shape": main["shape"],
                        "parallelism": f"dp{world} (independent particles, no collective)"},
             "roofline": {"bound": "hbm", "achieved": main["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
                          "frac": main["frac"],
                          "traffic": (args.traffic_per_update * n if args.traffic_per_update else None),
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per update, "
+                                           "4,194,304-particle capture scaled to n",
                          "peak_source": peak_src,
                          "bytes_per_update": main["bytes_per_update"]},
             "cpu_baseline": cpu,
@@ -417,7 +423,11 @@ def main():
                     help="scale of the 64-beam particle counts")
     ap.add_argument("--oracle-particles", type=int, default=512)
     ap.add_argument("--oracle-steps", type=int, default=50)
-    ap.add_argument("--traffic-per-update", type=float, default=None,
+    # DRAM bytes (read + write) per update of mc_step_tma_kernel<float, SoA, 16 warps>, from the
+    # ncu capture summarised in profiles/mc_step_tma_fp32_soa_4M.md (4,194,304 particles;
+    # the per-particle streams scale in proportion to n).  Re-measure whenever that kernel
+    # changes, and pass --traffic-per-update 0 to report null meanwhile.
+    ap.add_argument("--traffic-per-update", type=float, default=52.51,
                     help="DRAM bytes per update of the step kernel from an ncu capture (for roofline.traffic)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
