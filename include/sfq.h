@@ -202,7 +202,8 @@ typedef struct sfq_counters {
     unsigned long long blcfa_no_emission;/* threshold >= 0.75 gamma (Sec. 5) */
     unsigned long long blcfa_rejected;   /* rejected by Eq. rej_cond */
     unsigned long long timeouts;         /* bounded device waits that gave up (0 in a correct run) */
-    unsigned long long reserved[3];
+    unsigned long long surrogate_fallbacks; /* surrogate draws taken by the plain sampler */
+    unsigned long long reserved[2];
 } sfq_counters;
 
 /* One Monte Carlo step for every alive particle of `p` (Sec. 2 and 4; Sec. 5 for
@@ -262,6 +263,51 @@ sfq_status sfq_sort_products(sfq_ctx *ctx, const sfq_products *out, int64_t n, v
 #define SFQ_SORT_NOALLOC_MAX_N (1 << 20)
 #define SFQ_SORT_NOALLOC_SCRATCH_BYTES (44u << 20)
 sfq_status sfq_sort_products_noalloc(sfq_ctx *ctx, const sfq_products *out, int64_t n, void *stream);
+
+/* ---------------------------------------------------------------------------------
+ * Learned surrogate of the photon-emission inverse CDF (Sec. 4.3, Eq. again).
+ * A 2 -> 64 -> 64 -> 64 -> 1 SiLU network maps (ln chi, u) to the paper's inverse-CDF
+ * variable:  x1 = (ln chi - C) / S with C, S centring ln chi in [ln 1e-3, ln 100] on
+ * [-1, 1],  x2 = -ln(1 - u) / 8 - 1,  ln w-bar = network(x1, x2) + ln u,  and
+ * xi = s / (1 + s), s = 3 chi w-bar^3 / 2 (Eq. subs_altri).  Parameters are one binary32
+ * vector of sfq_mlp_num_params() = 8577 values, layer by layer, each layer its weights
+ * (row-major [out][in]) then its biases.  Inference rounds weights and the inputs of
+ * layers 2-4 to bfloat16 and accumulates in binary32; the two 64 x 64 layers run on the
+ * tensor cores.  Binary32 contexts only.  Device buffers are caller-owned; the object
+ * owns its parameters, optimiser state and calibration flags. */
+typedef struct sfq_mlp sfq_mlp;
+int32_t sfq_mlp_num_params(void);
+/* Parameters drawn from U(-1/sqrt(fan_in), 1/sqrt(fan_in)) with Philox(seed). */
+sfq_status sfq_mlp_create(sfq_ctx *ctx, uint64_t seed, sfq_mlp **out);
+void sfq_mlp_destroy(sfq_mlp *m);
+/* Copy the 8577 binary32 parameters to / from host memory (set resets the optimiser). */
+sfq_status sfq_mlp_get_params(sfq_mlp *m, float *host);
+sfq_status sfq_mlp_set_params(sfq_mlp *m, const float *host);
+/* Loss = sum_i (ln w_pred,i - lnw_i)^2 / n over n samples (binary32 device arrays chi,
+ * u in (0, 1), lnw = ln w-bar targets) and its gradient (device, 8577 floats); `loss`
+ * (device float) may be NULL.  quantize != 0 rounds as inference does (the rounding is
+ * passed straight through to the gradient).  Deterministic (fixed reduction order). */
+sfq_status sfq_mlp_loss_grad(sfq_mlp *m, int64_t n, const float *chi, const float *u, const float *lnw,
+                             int32_t quantize, float *grad, float *loss, void *stream);
+/* `steps` Adam steps (beta 0.9, 0.999, eps 1e-8) on minibatches of `batch` samples (a
+ * multiple of 64) drawn with replacement by Philox(seed, sample, step); learning rate
+ * lr * (1 + cos(pi t / steps)) / 2.  loss_history (device, `steps` floats) may be NULL. */
+sfq_status sfq_mlp_train(sfq_mlp *m, int64_t n, const float *chi, const float *u, const float *lnw, int64_t steps,
+                         int32_t batch, float lr, int32_t quantize, uint64_t seed, float *loss_history,
+                         void *stream);
+/* ln w-bar of the network (CUDA-core kernel, the same rounding as inference; no fallback). */
+sfq_status sfq_mlp_predict_lnw(sfq_mlp *m, int64_t n, const float *chi, const float *u, float *lnw, void *stream);
+/* Flags the cells of a 64 x 64 grid over (ln chi in [ln 1e-3, ln 100], u in (0, 1)) where
+ * |u_network - u| = |ln w_network - ln w_plain| / (d ln w_plain / du), over 8 x 8 points
+ * of the cell, exceeds tol_u (the plain fitted sampler of sfq_sample_photon_xi is the
+ * judge).  Returns the number of flagged cells and the largest error of the others.
+ * Synchronises `stream`. */
+sfq_status sfq_mlp_calibrate(sfq_mlp *m, float tol_u, int32_t *n_flagged, float *max_err, void *stream);
+/* As sfq_sample_photon_xi, through the network on the tensor cores.  With use_flags (after
+ * sfq_mlp_calibrate) draws in flagged cells, and every chi outside [1e-3, 100], take the
+ * plain sampler (counted in counters->surrogate_fallbacks). */
+sfq_status sfq_mlp_sample_photon_xi(sfq_mlp *m, int64_t n, const void *chi, const void *r, void *xi, void *xi_c,
+                                    int32_t use_flags, sfq_counters *counters, void *stream);
 
 /* Launch shape of sfq_mc_step for this context, the knob the autotuner turns.
  *   variant: 0 = automatic; 1 = warp-streaming kernel (each warp loads its particles

@@ -254,6 +254,14 @@ def itilde_pe_batch(w, chi):
     return out
 
 
+def itilde_pe_upper_batch(w, chi):
+    w, c = np.broadcast_arrays(_f64(w), _f64(chi))
+    w, c = _f64(w), _f64(c)
+    out = np.empty_like(w)
+    lib().orc_batch_itilde_pe_upper(_I64(w.size), _p(w), _p(c), _p(out))
+    return out
+
+
 def philox(ids, step, tag, seed):
     ids = np.ascontiguousarray(np.asarray(ids, dtype=np.uint64))
     out = np.empty((ids.size, 4), dtype=np.uint32)

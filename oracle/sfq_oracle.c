@@ -566,6 +566,10 @@ void orc_batch_itilde_pe(int64_t n, const double *w, const double *chi, double *
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t i = 0; i < n; ++i) out[i] = orc_itilde_pe(w[i], chi[i]);
 }
+void orc_batch_itilde_pe_upper(int64_t n, const double *w, const double *chi, double *out) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < n; ++i) out[i] = orc_itilde_pe_upper(w[i], chi[i]);
+}
 void orc_batch_itilde_pp(int64_t n, const double *v, const double *chi, double *out) {
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t i = 0; i < n; ++i) out[i] = orc_itilde_pp(v[i], chi[i]);

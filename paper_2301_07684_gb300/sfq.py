@@ -26,7 +26,8 @@ SFQ_FIELDS_SOA, SFQ_FIELDS_PLANE_WAVE = 0, 1
 STATUS = {0: "SFQ_OK", 1: "SFQ_ERR_ARG", 2: "SFQ_ERR_CUDA", 3: "SFQ_ERR_CAPACITY", 4: "SFQ_ERR_TABLE",
           5: "SFQ_ERR_RANGE", 6: "SFQ_ERR_TIMEOUT"}
 COUNTER_NAMES = ["updates", "events", "emitted", "pairs", "dropped", "spawn_dropped", "out_of_range",
-                 "nan_input", "gamma_below_one", "large_rdt", "blcfa_no_emission", "blcfa_rejected", "timeouts"]
+                 "nan_input", "gamma_below_one", "large_rdt", "blcfa_no_emission", "blcfa_rejected", "timeouts",
+                 "surrogate_fallbacks"]
 
 
 class Config(C.Structure):
@@ -98,6 +99,24 @@ def lib():
         L.sfq_sort_products.restype = st
         L.sfq_sort_products_noalloc.argtypes = [vp, C.POINTER(Products), i64, vp]
         L.sfq_sort_products_noalloc.restype = st
+        L.sfq_mlp_num_params.restype = C.c_int32
+        L.sfq_mlp_create.argtypes = [vp, C.c_uint64, C.POINTER(vp)]
+        L.sfq_mlp_create.restype = st
+        L.sfq_mlp_destroy.argtypes = [vp]
+        L.sfq_mlp_destroy.restype = None
+        for name in ("sfq_mlp_get_params", "sfq_mlp_set_params"):
+            getattr(L, name).argtypes = [vp, vp]
+            getattr(L, name).restype = st
+        L.sfq_mlp_loss_grad.argtypes = [vp, i64, vp, vp, vp, C.c_int32, vp, vp, vp]
+        L.sfq_mlp_loss_grad.restype = st
+        L.sfq_mlp_train.argtypes = [vp, i64, vp, vp, vp, i64, C.c_int32, C.c_float, C.c_int32, C.c_uint64, vp, vp]
+        L.sfq_mlp_train.restype = st
+        L.sfq_mlp_predict_lnw.argtypes = [vp, i64, vp, vp, vp, vp]
+        L.sfq_mlp_predict_lnw.restype = st
+        L.sfq_mlp_calibrate.argtypes = [vp, C.c_float, C.POINTER(C.c_int32), C.POINTER(C.c_float), vp]
+        L.sfq_mlp_calibrate.restype = st
+        L.sfq_mlp_sample_photon_xi.argtypes = [vp, i64, vp, vp, vp, vp, C.c_int32, vp, vp]
+        L.sfq_mlp_sample_photon_xi.restype = st
         L.sfq_set_step_shape.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
         L.sfq_set_step_shape.restype = st
         L.sfq_version.restype = C.c_char_p
@@ -108,6 +127,9 @@ def lib():
 EXPORTED = ["sfq_init", "sfq_finalize", "sfq_last_error", "sfq_constants", "sfq_photon_rate", "sfq_pair_rate",
             "sfq_uniforms", "sfq_sample_photon_xi", "sfq_sample_pair_xi", "sfq_mc_step", "sfq_mc_run",
             "sfq_autotune_step", "sfq_sort_scratch_bytes", "sfq_sort_products", "sfq_sort_products_noalloc", "sfq_set_step_shape",
+            "sfq_mlp_num_params", "sfq_mlp_create", "sfq_mlp_destroy", "sfq_mlp_get_params", "sfq_mlp_set_params",
+            "sfq_mlp_loss_grad", "sfq_mlp_train", "sfq_mlp_predict_lnw", "sfq_mlp_calibrate",
+            "sfq_mlp_sample_photon_xi",
             "sfq_version"]
 
 
@@ -266,6 +288,76 @@ class Context:
 
 SORT_NOALLOC_MAX_N = 1 << 20
 SORT_NOALLOC_SCRATCH_BYTES = 44 << 20
+
+
+class Surrogate:
+    """The learned inverse-CDF surrogate (sfq_mlp_*) of one binary32 context."""
+
+    def __init__(self, ctx: Context, seed=0):
+        self.ctx = ctx
+        h = C.c_void_p()
+        ctx._check(lib().sfq_mlp_create(ctx._h, seed, C.byref(h)), "sfq_mlp_create")
+        self._h = h
+
+    def close(self):
+        if self._h:
+            lib().sfq_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def num_params():
+        return int(lib().sfq_mlp_num_params())
+
+    def get_params(self):
+        import numpy as np
+        out = np.empty(self.num_params(), np.float32)
+        self.ctx._check(lib().sfq_mlp_get_params(self._h, out.ctypes.data_as(C.c_void_p)), "sfq_mlp_get_params")
+        return out
+
+    def set_params(self, theta):
+        import numpy as np
+        theta = np.ascontiguousarray(theta, np.float32)
+        assert theta.size == self.num_params()
+        self.ctx._check(lib().sfq_mlp_set_params(self._h, theta.ctypes.data_as(C.c_void_p)), "sfq_mlp_set_params")
+
+    def loss_grad(self, chi, u, lnw, quantize=False):
+        grad = torch.empty(self.num_params(), dtype=torch.float32, device=chi.device)
+        loss = torch.empty(1, dtype=torch.float32, device=chi.device)
+        self.ctx._check(lib().sfq_mlp_loss_grad(self._h, chi.numel(), _ptr(chi), _ptr(u), _ptr(lnw), int(quantize),
+                                                _ptr(grad), _ptr(loss), _stream()), "sfq_mlp_loss_grad")
+        return loss, grad
+
+    def train(self, chi, u, lnw, steps, batch=8192, lr=3e-3, quantize=True, seed=0, history=False):
+        hist = torch.empty(steps, dtype=torch.float32, device=chi.device) if history else None
+        self.ctx._check(lib().sfq_mlp_train(self._h, chi.numel(), _ptr(chi), _ptr(u), _ptr(lnw), steps, batch, lr,
+                                            int(quantize), seed, _ptr(hist), _stream()), "sfq_mlp_train")
+        return hist
+
+    def predict_lnw(self, chi, u):
+        out = torch.empty_like(chi)
+        self.ctx._check(lib().sfq_mlp_predict_lnw(self._h, chi.numel(), _ptr(chi), _ptr(u), _ptr(out), _stream()),
+                        "sfq_mlp_predict_lnw")
+        return out
+
+    def calibrate(self, tol_u=1e-3):
+        nf, mx = C.c_int32(0), C.c_float(0.0)
+        self.ctx._check(lib().sfq_mlp_calibrate(self._h, tol_u, C.byref(nf), C.byref(mx), _stream()),
+                        "sfq_mlp_calibrate")
+        return nf.value, mx.value
+
+    def sample_photon_xi(self, chi, r, use_flags=True, counters=None):
+        xi = torch.empty_like(chi)
+        xc = torch.empty_like(chi)
+        self.ctx._check(lib().sfq_mlp_sample_photon_xi(self._h, chi.numel(), _ptr(chi), _ptr(r), _ptr(xi), _ptr(xc),
+                                                       int(use_flags), _ptr(counters), _stream()),
+                        "sfq_mlp_sample_photon_xi")
+        return xi, xc
 
 
 def sort_scratch_bytes(n):

@@ -1,0 +1,220 @@
+"""GPU tests of the learned inverse-CDF surrogate (config 5).
+
+Workload: 2^22 training triples (chi log-uniform in [1e-3, 100], u = (k + 1/2) 2^-23
+uniform, ln w-bar from the oracle's dense CDF), training on the GPU by the library's own
+forward/backward kernels, calibration of the fallback cells against the plain sampler,
+then 2^26 draws through the tensor-core inference kernel judged by the KS distance of
+their probability-integral transform under the oracle's CDF (<= 1e-3).
+
+Tolerances (binary32 kernels against the FP64 oracle of the same network):
+- gradient, no rounding: |g - g_oracle| <= 1e-4 max|g_oracle| + 1e-3 |g_oracle|
+  (sums of 4096 binary32 products);
+- forward with bfloat16 rounding: a binary32 value that sits on a bfloat16 rounding
+  boundary may round the other way (one bfloat16 ulp, 2^-8 relative, in one
+  activation), so the network outputs agree to 2e-3 at worst and 1e-4 on average.
+"""
+import time
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+N_TRAIN = 1 << 22
+N_DRAWS = 1 << 26
+CHI_LO, CHI_HI = 1e-3, 100.0
+
+
+@pytest.fixture(scope="module")
+def dense():
+    from oracle import oracle as O
+    O.build()
+    from oracle import surrogate as S
+    T = S.DenseCDF()
+    # the fine table against direct quadrature at a few off-grid points
+    g = np.random.default_rng(11)
+    chi = np.exp(g.uniform(np.log(CHI_LO), np.log(CHI_HI), 24))
+    w = O.photon_wbar(g.uniform(0.01, 0.99, 24), chi)
+    lo, up = O.itilde_pe_batch(w, chi), O.itilde_pe_upper_batch(w, chi)
+    assert np.max(np.abs(T.cdf_w(chi, w) - lo / (lo + up))) < 5e-7
+    return T
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2301_07684_gb300 import build, sfq
+    build.build()
+    c = sfq.Context(ref_len_m=0.8e-6 / (2 * np.pi), dt=0.01, precision="fp32", seed=3)
+    yield c
+    c.close()
+
+
+def _draws(n, seed):
+    g = np.random.default_rng(seed)
+    chi = np.exp(g.uniform(np.log(CHI_LO), np.log(CHI_HI), n)).astype(np.float32)
+    u = ((g.integers(0, 1 << 23, n) + 0.5) / (1 << 23)).astype(np.float32)
+    return chi, u
+
+
+@pytest.fixture(scope="module")
+def trained(ctx, dense):
+    import torch
+    from paper_2301_07684_gb300 import sfq
+    chi, u = _draws(N_TRAIN, 21)
+    lnw = dense.inverse_lnw(chi.astype(np.float64), u.astype(np.float64)).astype(np.float32)
+    dev = ctx.device
+    tchi, tu, tl = (torch.as_tensor(a).to(dev) for a in (chi, u, lnw))
+    net = sfq.Surrogate(ctx, seed=7)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    hist = net.train(tchi, tu, tl, steps=30000, batch=8192, lr=3e-3, quantize=True, seed=9, history=True)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    nflag, max_err = net.calibrate(1e-3)
+    yield dict(net=net, hist=hist.cpu().numpy(), t_train=t_train, nflag=nflag, max_err=max_err)
+    net.close()
+
+
+def test_loss_grad_matches_oracle(ctx):
+    import torch
+    from oracle import surrogate as S
+    from paper_2301_07684_gb300 import sfq
+    net = sfq.Surrogate(ctx, seed=1)
+    g = np.random.default_rng(2)
+    theta = g.uniform(-0.4, 0.4, S.N_PARAMS).astype(np.float32)
+    net.set_params(theta)
+    n = 4096 + 37                                   # several blocks and a ragged tail
+    chi, u = _draws(n, 5)
+    lnw = g.normal(-1.0, 1.5, n).astype(np.float32)
+    dev = ctx.device
+    tchi, tu, tl = (torch.as_tensor(a).to(dev) for a in (chi, u, lnw))
+    for quantize in (False, True):
+        loss, grad = net.loss_grad(tchi, tu, tl, quantize=quantize)
+        lo, go = S.mlp_loss_grad(theta.astype(np.float64), np.log(chi.astype(np.float64)), u.astype(np.float64),
+                                 lnw.astype(np.float64), quantize=quantize)
+        gg = grad.cpu().numpy().astype(np.float64)
+        if not quantize:
+            assert abs(loss.item() - lo) <= 1e-5 * lo
+            assert np.all(np.abs(gg - go) <= 1e-4 * np.abs(go).max() + 1e-3 * np.abs(go)), \
+                np.max(np.abs(gg - go)) / np.abs(go).max()
+        else:
+            assert abs(loss.item() - lo) <= 1e-3 * lo
+            assert np.linalg.norm(gg - go) <= 1e-2 * np.linalg.norm(go)
+    # two calls give the same bits (fixed reduction order)
+    _, g1 = net.loss_grad(tchi, tu, tl)
+    _, g2 = net.loss_grad(tchi, tu, tl)
+    assert torch.equal(g1, g2)
+    net.close()
+
+
+def test_training_reduces_loss(trained):
+    h = trained["hist"]
+    assert np.all(np.isfinite(h))
+    assert h[-500:].mean() < 1e-3 * h[:10].mean(), (h[:10].mean(), h[-500:].mean())
+
+
+def test_forward_matches_oracle(ctx, trained):
+    import torch
+    from oracle import surrogate as S
+    net = trained["net"]
+    theta = net.get_params().astype(np.float64)
+    chi, u = _draws(20000, 31)
+    dev = ctx.device
+    got = net.predict_lnw(torch.as_tensor(chi).to(dev), torch.as_tensor(u).to(dev)).cpu().numpy().astype(np.float64)
+    ref = S.surrogate_lnw(theta, np.log(chi.astype(np.float64)), u.astype(np.float64), quantize=True)
+    d = np.abs(got - ref)
+    assert d.max() < 2e-3 and d.mean() < 1e-4, (d.max(), d.mean())
+
+
+def test_tensor_core_inference_matches_simt(ctx, trained):
+    import torch
+    net = trained["net"]
+    n = 3 * 128 * 152 + 55                          # several persistent rounds and a ragged tile
+    chi, u = _draws(n, 41)
+    dev = ctx.device
+    tchi, tu = torch.as_tensor(chi).to(dev), torch.as_tensor(u).to(dev)
+    xi, xc = net.sample_photon_xi(tchi, tu, use_flags=False)
+    lnw_simt = net.predict_lnw(tchi, tu).cpu().numpy().astype(np.float64)
+    s = xi.cpu().numpy().astype(np.float64) / xc.cpu().numpy().astype(np.float64)
+    lnw_tc = (np.log(2.0 * s) - np.log(3.0 * chi.astype(np.float64))) / 3.0
+    d = np.abs(lnw_tc - lnw_simt)
+    assert d.max() < 2e-3 and d.mean() < 1e-4, (d.max(), d.mean())
+
+
+def test_inference_edges(ctx, trained):
+    import torch
+    from paper_2301_07684_gb300 import sfq
+    net = trained["net"]
+    dev = ctx.device
+    chi = torch.tensor([1.0, 1e-4, 500.0, -1.0, 1.0, 1.0, 0.5, 0.5], dtype=torch.float32, device=dev)
+    u = torch.tensor([0.5, 0.5, 0.5, 0.5, 0.0, 1.0, 0.3, 0.7], dtype=torch.float32, device=dev)
+    cnt = sfq.counters_tensor(dev)
+    xi, xc = net.sample_photon_xi(chi, u, use_flags=True, counters=cnt)
+    c = sfq.counters_dict(cnt)
+    x = xi.cpu().numpy()
+    assert c["nan_input"] == 3 and np.all(x[3:6] == 0.0)
+    assert c["surrogate_fallbacks"] >= 2                       # chi outside [1e-3, 100]
+    ref, _ = ctx.sample_photon_xi(chi[:3], u[:3])
+    np.testing.assert_array_equal(x[1:3], ref.cpu().numpy()[1:3])   # fallbacks are the plain sampler
+    assert np.all((x[[0, 6, 7]] > 0) & (x[[0, 6, 7]] < 1))
+    # empty input is a no-op
+    e = torch.empty(0, dtype=torch.float32, device=dev)
+    net.sample_photon_xi(e, e)
+
+
+def _ks(p):
+    p = np.sort(p)
+    n = p.size
+    i = np.arange(n, dtype=np.float64)
+    return max(np.max((i + 1) / n - p), np.max(p - i / n))
+
+
+def test_config5_ks_and_gain(ctx, trained, dense):
+    """2^26 draws: KS of F_oracle(xi | chi) against U(0,1) <= 1e-3 with the fallback cells
+    in use; the network's footprint against the plain table's; times of both paths."""
+    import torch
+    from paper_2301_07684_gb300 import sfq
+    net = trained["net"]
+    dev = ctx.device
+    chi, u = _draws(N_DRAWS, 51)
+    tchi, tu = torch.as_tensor(chi).to(dev), torch.as_tensor(u).to(dev)
+    cnt = sfq.counters_tensor(dev)
+    net.sample_photon_xi(tchi, tu, use_flags=True, counters=cnt)            # warm-up
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    xi, xc = net.sample_photon_xi(tchi, tu, use_flags=True, counters=cnt)
+    ev[1].record()
+    xp, xpc = ctx.sample_photon_xi(tchi, tu)
+    ev[2].record()
+    xi_raw, xc_raw = net.sample_photon_xi(tchi, tu, use_flags=False)
+    ev[3].record()
+    torch.cuda.synchronize()
+    t_net, t_plain = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    c = sfq.counters_dict(cnt)
+    lnchi = np.log(chi.astype(np.float64))
+
+    def pit(a, b):
+        out = np.empty(N_DRAWS)
+        for k in range(0, N_DRAWS, 1 << 23):
+            sl = slice(k, k + (1 << 23))
+            s = a[sl].cpu().numpy().astype(np.float64) / b[sl].cpu().numpy().astype(np.float64)
+            lnw = (np.log(2.0 * s) - np.log(3.0) - lnchi[sl]) / 3.0
+            z = dense.logit(lnchi[sl], lnw)
+            out[sl] = 1.0 / (1.0 + np.exp(-z))
+        return out
+
+    ks_net = _ks(pit(xi, xc))
+    ks_plain = _ks(pit(xp, xpc))
+    ks_raw = _ks(pit(xi_raw, xc_raw))
+    frac_fb = c["surrogate_fallbacks"] / N_DRAWS
+    table_bytes = 54027 * 4                                   # nlc_inv binary32 coefficients
+    net_bytes = sfq.Surrogate.num_params() * 2                # bfloat16 weights
+    print(f"\nsurrogate: KS {ks_net:.2e} (raw network {ks_raw:.2e}, plain sampler {ks_plain:.2e}); "
+          f"flagged cells {trained['nflag']}/4096, fallback fraction {frac_fb:.4f}, "
+          f"max unflagged cell error {trained['max_err']:.2e}; training {trained['t_train']:.1f} s; "
+          f"2^26 draws: network {t_net:.2f} ms, plain {t_plain:.2f} ms; "
+          f"footprint {net_bytes} B vs {table_bytes} B")
+    assert ks_net <= 1e-3, ks_net
+    assert ks_plain <= 1e-3, ks_plain
+    assert frac_fb < 0.5
+    assert net_bytes * 10 < table_bytes
