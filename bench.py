@@ -306,11 +306,84 @@ def run_ours(args):
         torch.cuda.empty_cache()
         return out_b
 
+    def surrogate_leg():
+        """Config 5: the learned inverse-CDF surrogate.  Trained on the GPU (the library's own
+        forward/backward/Adam kernels) on 2^22 triples whose targets come from the plain
+        fitted sampler, calibrated against it, then timed on 2^26 draws beside the plain
+        sampler and the CUDA-core forward."""
+        ctx = sfq.Context(ref_len_m=W.REF_LEN, dt=W.DT, precision="fp32", seed=5, device=local)
+        net = sfq.Surrogate(ctx, seed=7)
+        g = np.random.Generator(np.random.Philox(1000 + rank))
+        nt = 1 << 22
+        chi_t = torch.as_tensor(np.exp(g.uniform(np.log(1e-3), np.log(100.0), nt)).astype(np.float32)).to(device)
+        u_t = torch.as_tensor(((g.integers(0, 1 << 23, nt) + 0.5) / (1 << 23)).astype(np.float32)).to(device)
+        lnw_t = net.plain_targets(chi_t, u_t)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps_train = args.surrogate_steps
+        torch.cuda.synchronize()
+        e0.record()
+        net.train(chi_t, u_t, lnw_t, steps=steps_train, batch=8192, lr=3e-3, quantize=True, seed=9)
+        e1.record()
+        torch.cuda.synchronize()
+        train_ms = e0.elapsed_time(e1)
+        nflag, max_err = net.calibrate(1e-3)
+        nd = 1 << 26
+        chi_d = torch.as_tensor(np.exp(g.uniform(np.log(1e-3), np.log(100.0), nd)).astype(np.float32)).to(device)
+        u_d = torch.as_tensor(((g.integers(0, 1 << 23, nd) + 0.5) / (1 << 23)).astype(np.float32)).to(device)
+        cnt = sfq.counters_tensor(device)
+
+        def timed(fn, reps=5):
+            fn()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(reps):
+                e0.record()
+                fn()
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return statistics.median(ts)
+
+        t_tc = timed(lambda: net.sample_photon_xi(chi_d, u_d, use_flags=True, counters=cnt))
+        t_tc_raw = timed(lambda: net.sample_photon_xi(chi_d, u_d, use_flags=False))
+        t_simt = timed(lambda: net.predict_lnw(chi_d, u_d))
+        t_plain = timed(lambda: ctx.sample_photon_xi(chi_d, u_d))
+        c = sfq.counters_dict(cnt)
+        flop_per_sample = 2 * (2 * 64 * 64)            # the two 64 x 64 layers on the tensor cores
+        tflops = nd * flop_per_sample / (t_tc_raw * 1e-3) / 1e12
+        bf16_peak = None
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+                bf16_peak = float(json.load(fh)["bf16_tflops"])
+        except Exception:
+            pass
+        out_s = {"workload": "2^22 training triples (targets from the plain sampler), 2^26 draws, "
+                             "chi log-uniform in [1e-3, 100], u uniform",
+                 "train_steps": steps_train, "train_batch": 8192, "train_ms": train_ms,
+                 "calibration": {"tol_u": 1e-3, "flagged_cells": nflag, "cells": 4096,
+                                 "max_unflagged_err_u": max_err},
+                 "draws": nd, "value": nd / (t_tc * 1e-3), "unit": "samples/s", "ms": t_tc,
+                 "fallback_fraction": c["surrogate_fallbacks"] / (6 * nd),
+                 "network_only": {"ms": t_tc_raw, "samples_per_s": nd / (t_tc_raw * 1e-3),
+                                  "tensor_tflops": tflops,
+                                  "tensor_frac_of_measured_bf16": (tflops / bf16_peak) if bf16_peak else None},
+                 "cuda_core_forward": {"ms": t_simt, "samples_per_s": nd / (t_simt * 1e-3)},
+                 "plain_sampler": {"ms": t_plain, "samples_per_s": nd / (t_plain * 1e-3)},
+                 "footprint_bytes": {"network_bf16": sfq.Surrogate.num_params() * 2,
+                                     "plain_table_f32": 54027 * 4},
+                 "bound": "alu (SFU: two exponential/reciprocal per SiLU, 192 SiLU per draw)"}
+        net.close()
+        ctx.close()
+        del chi_t, u_t, lnw_t, chi_d, u_d
+        torch.cuda.empty_cache()
+        return out_s
+
     main = one_path("fp32", "soa", args.steps, args.warmup, with_e2e=True)
     pw = one_path("fp32", "pw", args.steps, args.warmup, with_e2e=False)
     f64_steps = max(2, args.steps // 10)
     f64 = one_path("fp64", "soa", f64_steps, max(3, min(args.warmup, 3)), with_e2e=False)
     batched = batched_leg() if args.batched_steps > 0 else None
+    surrogate = surrogate_leg() if args.surrogate_steps > 0 else None
 
     # max over ranks of the headline time
     t = torch.tensor([main["ms_per_step"]], device=device)
@@ -348,6 +421,7 @@ def run_ours(args):
                                   "achieved_gbs": pw["achieved_gbs"], "frac": pw["frac"],
                                   "bytes_per_update": pw["bytes_per_update"]},
             "batched": batched,
+            "surrogate": surrogate,
             "events_per_update": main["events_per_update"],
             "device": dev_name,
         }
@@ -421,6 +495,8 @@ def main():
                     help="steps of the 64-beam batched run in one CUDA graph (0 skips it)")
     ap.add_argument("--batched-scale", type=float, default=1.0,
                     help="scale of the 64-beam particle counts")
+    ap.add_argument("--surrogate-steps", type=int, default=30000,
+                    help="training steps of the surrogate leg (0 skips it)")
     ap.add_argument("--oracle-particles", type=int, default=512)
     ap.add_argument("--oracle-steps", type=int, default=50)
     # DRAM bytes (read + write) per update of mc_step_tma_kernel<float, SoA, 16 warps>, from the

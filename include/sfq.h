@@ -297,6 +297,9 @@ sfq_status sfq_mlp_train(sfq_mlp *m, int64_t n, const float *chi, const float *u
                          void *stream);
 /* ln w-bar of the network (CUDA-core kernel, the same rounding as inference; no fallback). */
 sfq_status sfq_mlp_predict_lnw(sfq_mlp *m, int64_t n, const float *chi, const float *u, float *lnw, void *stream);
+/* Training targets from the plain fitted sampler: lnw = ln w-bar with s = 3 chi w-bar^3 / 2
+ * the value sfq_sample_photon_xi uses (for training without oracle data). */
+sfq_status sfq_mlp_plain_targets(sfq_mlp *m, int64_t n, const float *chi, const float *u, float *lnw, void *stream);
 /* Flags the cells of a 64 x 64 grid over (ln chi in [ln 1e-3, ln 100], u in (0, 1)) where
  * |u_network - u| = |ln w_network - ln w_plain| / (d ln w_plain / du), over 8 x 8 points
  * of the cell, exceeds tol_u (the plain fitted sampler of sfq_sample_photon_xi is the

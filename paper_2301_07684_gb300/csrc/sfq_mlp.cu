@@ -412,6 +412,13 @@ __global__ void __launch_bounds__(64) calibrate_kernel(const float *__restrict__
     }
 }
 
+// ln w-bar of the plain fitted sampler (training targets without the oracle).
+__global__ void plain_targets_kernel(const float *__restrict__ inv, int64_t n, const float *__restrict__ chi,
+                                     const float *__restrict__ u, float *__restrict__ lnw) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        lnw[i] = plain_lnw(inv, chi[i], u[i]);
+}
+
 // ---------------------------------------------------------------------------------------
 // Tensor-core inference.  One block of 128 threads handles tiles of 128 samples (one
 // sample per thread, one row of the 128 x 64 activation tile).  Layers 2 and 3 are
@@ -840,6 +847,20 @@ sfq_status sfq_mlp_predict_lnw(sfq_mlp *m, int64_t n, const float *chi, const fl
     predict_kernel<<<grid, 128, 0, (cudaStream_t)stream>>>(m->params, n, chi, u, lnw);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SFQ_OK : cuda_fail(m->ctx, e, "sfq_mlp_predict_lnw");
+}
+
+sfq_status sfq_mlp_plain_targets(sfq_mlp *m, int64_t n, const float *chi, const float *u, float *lnw, void *stream) {
+    if (!m) return SFQ_ERR_ARG;
+    if (n < 0) return fail(m->ctx, SFQ_ERR_ARG, "n < 0");
+    if (n == 0) return SFQ_OK;
+    if (!chi || !u || !lnw) return fail(m->ctx, SFQ_ERR_ARG, "null buffer");
+    DeviceGuard g(m->ctx->device);
+    const int64_t blocks = (n + 255) / 256;
+    const int grid = (int)(blocks < (int64_t)m->ctx->num_sms * 8 ? blocks : (int64_t)m->ctx->num_sms * 8);
+    plain_targets_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(static_cast<const float *>(m->ctx->d_nlc_inv), n,
+                                                                 chi, u, lnw);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SFQ_OK : cuda_fail(m->ctx, e, "sfq_mlp_plain_targets");
 }
 
 sfq_status sfq_mlp_calibrate(sfq_mlp *m, float tol_u, int32_t *n_flagged, float *max_err, void *stream) {

@@ -113,6 +113,8 @@ def lib():
         L.sfq_mlp_train.restype = st
         L.sfq_mlp_predict_lnw.argtypes = [vp, i64, vp, vp, vp, vp]
         L.sfq_mlp_predict_lnw.restype = st
+        L.sfq_mlp_plain_targets.argtypes = [vp, i64, vp, vp, vp, vp]
+        L.sfq_mlp_plain_targets.restype = st
         L.sfq_mlp_calibrate.argtypes = [vp, C.c_float, C.POINTER(C.c_int32), C.POINTER(C.c_float), vp]
         L.sfq_mlp_calibrate.restype = st
         L.sfq_mlp_sample_photon_xi.argtypes = [vp, i64, vp, vp, vp, vp, C.c_int32, vp, vp]
@@ -128,7 +130,7 @@ EXPORTED = ["sfq_init", "sfq_finalize", "sfq_last_error", "sfq_constants", "sfq_
             "sfq_uniforms", "sfq_sample_photon_xi", "sfq_sample_pair_xi", "sfq_mc_step", "sfq_mc_run",
             "sfq_autotune_step", "sfq_sort_scratch_bytes", "sfq_sort_products", "sfq_sort_products_noalloc", "sfq_set_step_shape",
             "sfq_mlp_num_params", "sfq_mlp_create", "sfq_mlp_destroy", "sfq_mlp_get_params", "sfq_mlp_set_params",
-            "sfq_mlp_loss_grad", "sfq_mlp_train", "sfq_mlp_predict_lnw", "sfq_mlp_calibrate",
+            "sfq_mlp_loss_grad", "sfq_mlp_train", "sfq_mlp_predict_lnw", "sfq_mlp_plain_targets", "sfq_mlp_calibrate",
             "sfq_mlp_sample_photon_xi",
             "sfq_version"]
 
@@ -343,6 +345,12 @@ class Surrogate:
         out = torch.empty_like(chi)
         self.ctx._check(lib().sfq_mlp_predict_lnw(self._h, chi.numel(), _ptr(chi), _ptr(u), _ptr(out), _stream()),
                         "sfq_mlp_predict_lnw")
+        return out
+
+    def plain_targets(self, chi, u):
+        out = torch.empty_like(chi)
+        self.ctx._check(lib().sfq_mlp_plain_targets(self._h, chi.numel(), _ptr(chi), _ptr(u), _ptr(out), _stream()),
+                        "sfq_mlp_plain_targets")
         return out
 
     def calibrate(self, tol_u=1e-3):

@@ -1,0 +1,88 @@
+"""Multi-rank sharding on the CPU (gloo, world size 2): each rank runs the oracle over its
+contiguous share of the particle ids, the records and counters are gathered, and the
+union equals the unsplit run record for record (the random numbers are keyed by the
+particle id, so the split changes nothing)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from paper_2301_07684_gb300 import shard
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _case():
+    from paper_2301_07684_gb300 import workloads as W
+    d = W.config2(n=40, seed=2)
+    nsteps = 30
+    E = np.zeros((40, nsteps, 6))
+    for j in range(nsteps):
+        (ex, ey, ez), (bx, by, bz) = W.plane_wave_fields(d["k0"], d["amp0"], d["table"], j)
+        E[:, j, 1], E[:, j, 5] = ey, bz
+    p = np.stack([d["px"], d["py"], d["pz"]], 1).astype(np.float64)
+    return d, p, E, nsteps
+
+
+def _run(ids, d, p, E, nsteps):
+    from oracle import oracle as O
+    from paper_2301_07684_gb300 import workloads as W
+    r = O.mc_run(p[ids], d["tau"][ids], ids.astype(np.uint64), d["flags"][ids], (d["flags"][ids] >> 2) & 3, E[ids],
+                 rho=W.RHO, dt=W.DT, seed=99, nsteps=nsteps, near_od=1e-6)
+    pr = r["products"]
+    rec = dict(px=pr["p"][:, 0], py=pr["p"][:, 1], pz=pr["p"][:, 2], parent_id=pr["parent_id"],
+               step=pr["step"].astype(np.uint32),
+               meta=((pr["member"] << 2) | (pr["parent_tag"] << 4) | (pr["species"] << 6)).astype(np.uint8))
+    return rec, {"events": int(r["n_events"].sum()), "records": len(pr)}, r
+
+
+def _worker(rank, world, port, out_dir):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    d, p, E, nsteps = _case()
+    a, b = shard.shard_bounds(len(p), rank, world)
+    rec, cnt, r = _run(np.arange(a, b), d, p, E, nsteps)
+    merged, total = shard.gather(rec, cnt)
+    if rank == 0:
+        np.savez(os.path.join(out_dir, "merged.npz"), **merged, events=total["events"], records=total["records"])
+    np.save(os.path.join(out_dir, f"final{rank}.npy"), r["p"])
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_shard_bounds_cover_the_range():
+    for n in (0, 1, 7, 1000):
+        for world in (1, 2, 3, 8):
+            edges = [shard.shard_bounds(n, r, world) for r in range(world)]
+            assert edges[0][0] == 0 and edges[-1][1] == n
+            assert all(edges[k][1] == edges[k + 1][0] for k in range(world - 1))
+            sizes = [b - a for a, b in edges]
+            assert max(sizes) - min(sizes) <= 1
+    with pytest.raises(ValueError):
+        shard.shard_bounds(10, 2, 2)
+
+
+def test_two_gloo_ranks_equal_the_single_run(tmp_path):
+    import torch.multiprocessing as mp
+    from oracle import oracle as O
+    O.build()
+    port = _free_port()
+    mp.start_processes(_worker, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    got = np.load(tmp_path / "merged.npz")
+    d, p, E, nsteps = _case()
+    rec, cnt, r = _run(np.arange(len(p)), d, p, E, nsteps)
+    ref = shard.merge_records([rec])
+    assert int(got["records"]) == cnt["records"] > 10 and int(got["events"]) == cnt["events"]
+    for k in shard.RECORD_COLUMNS:
+        np.testing.assert_array_equal(got[k], ref[k], err_msg=k)
+    final = np.concatenate([np.load(tmp_path / "final0.npy"), np.load(tmp_path / "final1.npy")])
+    np.testing.assert_array_equal(final, r["p"])
