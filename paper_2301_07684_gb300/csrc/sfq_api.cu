@@ -6,7 +6,9 @@
 #include <cstring>
 #include <new>
 
+#include "sfq_device.cuh"
 #include "sfq_internal.h"
+#include "sfq_tables_layout.h"
 
 namespace {
 
@@ -150,10 +152,29 @@ sfq_status sfq_init(const sfq_config *cfg, sfq_ctx **out) {
                              t.ki13_bytes};
     void **dst[6] = {&ctx->d_nlc_rate, &ctx->d_nbw_rate, &ctx->d_nlc_inv, &ctx->d_nbw_inv, &ctx->d_k23,
                      &ctx->d_ki13};
+    // the 2-D inverse-CDF tables (k = 2, 3) go to the device with every row of a piece
+    // padded to 16 bytes, the layout the kernels read with vector loads
+    const bool f64 = cfg->precision == SFQ_FP64;
+    const size_t esz = f64 ? 8 : 4;
+    const int row[6] = {0, 0, (f64 ? NLC_INV_F64_DY : NLC_INV_F32_DY) + 1, (f64 ? NBW_INV_F64_DY : NBW_INV_F32_DY) + 1,
+                        0, 0};
     for (int k = 0; k < 6; ++k) {
         if (!src[k] || bytes[k] == 0) { sfq_finalize(ctx); return SFQ_ERR_TABLE; }
-        e = cudaMalloc(dst[k], bytes[k]);
-        if (e == cudaSuccess) e = cudaMemcpy(*dst[k], src[k], bytes[k], cudaMemcpyHostToDevice);
+        std::vector<unsigned char> padded;
+        const void *h = src[k];
+        size_t nb = bytes[k];
+        if (row[k] > 0) {
+            const size_t rb = row[k] * esz, pb = sfq::padded_row(row[k], (int)esz) * esz;
+            if (bytes[k] % rb) { sfq_finalize(ctx); return SFQ_ERR_TABLE; }
+            const size_t rows = bytes[k] / rb;
+            padded.assign(rows * pb, 0);
+            for (size_t r = 0; r < rows; ++r)
+                std::memcpy(padded.data() + r * pb, static_cast<const unsigned char *>(src[k]) + r * rb, rb);
+            h = padded.data();
+            nb = padded.size();
+        }
+        e = cudaMalloc(dst[k], nb);
+        if (e == cudaSuccess) e = cudaMemcpy(*dst[k], h, nb, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { sfq_finalize(ctx); return SFQ_ERR_CUDA; }
     }
     *out = ctx;

@@ -168,16 +168,36 @@ __device__ __forceinline__ T horner1(const T *c, T x) {
     return acc;
 }
 
-// sum_ij c[i*(DY+1)+j] x^i y^j: Horner in y for each i, then in x.  `c` is read
-// through the read-only data cache.
+// Row length, in elements, of a 2-D table piece whose rows of n coefficients are padded
+// to a multiple of 16 bytes (so that a row is read with vector loads).
+__host__ __device__ constexpr int padded_row(int n, int esz) { return (n * esz + 15) / 16 * 16 / esz; }
+
+// Vector load of V = 16/sizeof(T) consecutive coefficients through the read-only cache.
+__device__ __forceinline__ void ldg_vec(const float *p, float *d) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+}
+__device__ __forceinline__ void ldg_vec(const double *p, double *d) {
+    const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+    d[0] = v.x; d[1] = v.y;
+}
+
+// sum_ij c[i*ROW+j] x^i y^j, i <= DX, j <= DY: Horner in y for each row i, then in x.
+// Rows are ROW = padded_row(DY + 1) elements apart (16-byte aligned) and each is read
+// with ROW / V vector loads.
 template <int DX, int DY, typename T>
 __device__ __forceinline__ T horner2(const T *__restrict__ c, T x, T y) {
+    constexpr int ROW = padded_row(DY + 1, (int)sizeof(T));
+    constexpr int V = 16 / (int)sizeof(T);
     T acc = (T)0;
 #pragma unroll
     for (int i = DX; i >= 0; --i) {
-        T b = __ldg(c + i * (DY + 1) + DY);
+        T co[ROW];
 #pragma unroll
-        for (int j = DY - 1; j >= 0; --j) b = fma(b, y, __ldg(c + i * (DY + 1) + j));
+        for (int k = 0; k < ROW / V; ++k) ldg_vec(c + i * ROW + k * V, co + k * V);
+        T b = co[DY];
+#pragma unroll
+        for (int j = DY - 1; j >= 0; --j) b = fma(b, y, co[j]);
         acc = (i == DX) ? b : fma(acc, x, b);
     }
     return acc;

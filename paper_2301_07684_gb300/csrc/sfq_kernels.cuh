@@ -148,7 +148,7 @@ __device__ __forceinline__ T photon_s(const T *__restrict__ inv, T chi, T r, boo
     bool low;
     const int ic = octave_piece<T, Q::PI_XELO, Q::PI_XEHI, Q::PI_XSUB, Q::PI_XLOW, Q::PI_XSUBLOW>(chi, xc, oor);
     const int ir = prob_piece<T, Q::PI_YE0, Q::PI_YSUB, Q::PI_YSUBLOW, Q::PI_YQLO, Q::PI_YSUBQ>(r, xr, low, oor);
-    const T *c = inv + ((size_t)ic * Q::PI_NY + ir) * ((Q::PI_DX + 1) * (Q::PI_DY + 1));
+    const T *c = inv + ((size_t)ic * Q::PI_NY + ir) * ((Q::PI_DX + 1) * padded_row(Q::PI_DY + 1, sizeof(T)));
     T w = horner2<Q::PI_DX, Q::PI_DY>(c, xc, xr);
     if (low) w *= r;                          // the low-r block holds w-bar / r
     const T chi_eff = chi > (T)4096 ? (T)4096 : chi;
@@ -166,7 +166,7 @@ __device__ __forceinline__ void pair_shares(const T *__restrict__ inv, T chi, T 
     bool low;
     const int ic = octave_piece<T, Q::PP_XELO, Q::PP_XEHI, Q::PP_XSUB, Q::PP_XLOW, Q::PP_XSUBLOW>(chi, xc, oor);
     const int ir = prob_piece<T, Q::PP_YE0, Q::PP_YSUB, Q::PP_YSUBLOW, Q::PP_YQLO, Q::PP_YSUBQ>(a, xr, low, oor);
-    const T *c = inv + ((size_t)ic * Q::PP_NY + ir) * ((Q::PP_DX + 1) * (Q::PP_DY + 1));
+    const T *c = inv + ((size_t)ic * Q::PP_NY + ir) * ((Q::PP_DX + 1) * padded_row(Q::PP_DY + 1, sizeof(T)));
     const T y = horner2<Q::PP_DX, Q::PP_DY>(c, xc, xr);
     const T small = (T)0.5 * y, big = (T)1 - small;
     if (rp >= (T)0) { xe = big; xp = small; }

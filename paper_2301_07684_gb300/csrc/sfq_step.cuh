@@ -61,11 +61,15 @@ struct StepArgs {
     sfq_counters *counters;
 };
 
+// Entry of the TMA-staged kernel's event queue: the particle's state as the step read it,
+// so that the event path re-reads nothing from global memory.
 template <typename T>
 struct QEntry {
     int64_t i;          // particle index
     T g;                // energy of the particle
     T chi;              // quantum parameter at the event
+    T px, py, pz;       // momentum before the event
+    uint32_t fl;        // flags
 };
 // Entry of the warp-streaming kernel, which also serves beyond-LCFA leptons.
 template <typename T>
@@ -232,62 +236,11 @@ __device__ __forceinline__ bool blcfa_phase_a(const StepArgs<T> &a, const T *s_n
     return true;
 }
 
-// One batch of up to 32 queued events, one per lane (lanes >= nvalid idle); all
-// 32 lanes execute it (warp shuffles).  Sampling (Eq. again / Eq. again_pp),
-// parent update and product records; one global atomic per batch reserves the
-// records.
-template <typename T, typename E>
-__device__ __forceinline__ void process_events(const StepArgs<T> &a, const E &e, T e_aux, bool valid, Cnt &c) {
+// Warp-collective reservation of nprod product records and nspawn children per lane:
+// one atomic per counter for the warp; returns each lane's first index.
+__device__ __forceinline__ void reserve_records(unsigned long long *ocount, unsigned long long *scount, int nprod,
+                                                int nspawn, unsigned long long &bp, unsigned long long &bs) {
     const int lane = threadIdx.x & 31;
-    int nprod = 0, nspawn = 0;
-    T px = 0, py = 0, pz = 0, xa = 0, xb = 0;
-    uint8_t fl = 0;
-    uint64_t id = 0;
-    uint32_t tag = 0;
-    bool photon = false;
-    bool oor = false;
-    if (valid) {
-        fl = a.flags[e.i];
-        id = a.id ? a.id[e.i] : a.id_base + (uint64_t)e.i;
-        tag = (fl >> SFQ_TAG_SHIFT) & 3u;
-        px = a.px[e.i]; py = a.py[e.i]; pz = a.pz[e.i];
-        photon = ((fl >> SFQ_SPECIES_SHIFT) & 3) == SFQ_PHOTON;
-        const u4 w = draws(a.seed, id, a.step, tag);
-        const T r1 = uniform<T>(w.w[1]);
-        if (photon) {
-            ++c.v[C_EV];
-            pair_shares<T>(a.tab.nbw_inv, e.chi, r1, xa, xb, oor);
-            nprod = 2;
-            nspawn = a.scount ? 2 : 0;
-            ++c.v[C_PAIR];
-        } else if (e_aux < (T)0) {
-            ++c.v[C_EV];
-            xa = photon_s<T>(a.tab.nlc_inv, e.chi, r1, oor);      // s
-            xb = uniform<T>(w.w[0]);                               // for the fresh optical depth
-            nprod = 1;
-            ++c.v[C_EMIT];
-        } else {
-            // beyond-LCFA: LCFA sample, then the rejection of Eq. rej_cond below gamma_LCFA
-            xa = photon_s<T>(a.tab.nlc_inv, e.chi, r1, oor);
-            xb = (T)-1;                                            // marks: no optical depth
-            bool accept = true;
-            const T gbar = e.g * xa / ((T)1 + xa);
-            if (e_aux > (T)0 && !(gbar > e_aux)) {
-                const T uL = e_aux / (e.g - e_aux);
-                const T lhs = log(uniform<T>(w.w[2])) + ln_spectrum<T>(a.tab.k23, a.tab.ki13, xa, e.chi, oor);
-                const T rhs = ln_spectrum<T>(a.tab.k23, a.tab.ki13, uL, e.chi, oor);
-                accept = lhs <= rhs;
-            }
-            if (accept) {
-                nprod = 1;
-                ++c.v[C_EMIT];
-            } else {
-                ++c.v[C_REJ];
-            }
-        }
-        c.v[C_OOR] += oor;
-    }
-    // warp prefix sums of the record counts
     int pre_p = nprod, pre_s = nspawn;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -297,20 +250,80 @@ __device__ __forceinline__ void process_events(const StepArgs<T> &a, const E &e,
     }
     const int tot_p = __shfl_sync(0xFFFFFFFFu, pre_p, 31);
     const int tot_s = __shfl_sync(0xFFFFFFFFu, pre_s, 31);
-    unsigned long long bp = 0, bs = 0;
+    unsigned long long b0 = 0, b1 = 0;
     if (lane == 31) {
-        if (tot_p) bp = atomicAdd(a.ocount, (unsigned long long)tot_p);
-        if (tot_s) bs = atomicAdd(a.scount, (unsigned long long)tot_s);
+        if (tot_p) b0 = atomicAdd(ocount, (unsigned long long)tot_p);
+        if (tot_s) b1 = atomicAdd(scount, (unsigned long long)tot_s);
     }
-    bp = __shfl_sync(0xFFFFFFFFu, bp, 31) + (unsigned long long)(pre_p - nprod);
-    bs = __shfl_sync(0xFFFFFFFFu, bs, 31) + (unsigned long long)(pre_s - nspawn);
+    bp = __shfl_sync(0xFFFFFFFFu, b0, 31) + (unsigned long long)(pre_p - nprod);
+    bs = __shfl_sync(0xFFFFFFFFu, b1, 31) + (unsigned long long)(pre_s - nspawn);
+}
+
+// One batch of up to 32 queued events, one per lane (lanes with valid = false idle); all
+// 32 lanes execute it (warp shuffles).  The lane receives the particle's index i, its
+// energy g, chi at the event, aux (-1 for an optical-depth event; for beyond-LCFA,
+// gamma_LCFA or 0), and the momentum and flags the step read.  Sampling (Eq. again /
+// Eq. again_pp), parent update and product records.  The records are reserved with one
+// global atomic per batch, before the sampling when every record count is known up
+// front (no beyond-LCFA lane, whose emission may be rejected), so that the atomic's
+// latency overlaps the sampling.
+template <typename T>
+__device__ __forceinline__ void process_events(const StepArgs<T> &a, int64_t ei, T eg, T echi, T e_aux, T px,
+                                               T py, T pz, uint8_t fl, bool valid, Cnt &c) {
+    const bool photon = valid && ((fl >> SFQ_SPECIES_SHIFT) & 3) == SFQ_PHOTON;
+    const bool maybe = valid && !photon && !(e_aux < (T)0);        // beyond-LCFA: may be rejected
+    const bool late = __any_sync(0xFFFFFFFFu, maybe);
+    int nprod = valid ? (photon ? 2 : 1) : 0;
+    int nspawn = photon && a.scount ? 2 : 0;
+    unsigned long long bp = 0, bs = 0;
+    if (!late) reserve_records(a.ocount, a.scount, nprod, nspawn, bp, bs);
+    T xa = 0, xb = 0;
+    uint64_t id = 0;
+    uint32_t tag = 0;
+    bool oor = false;
+    if (valid) {
+        id = a.id ? a.id[ei] : a.id_base + (uint64_t)ei;
+        tag = (fl >> SFQ_TAG_SHIFT) & 3u;
+        const u4 w = draws(a.seed, id, a.step, tag);
+        const T r1 = uniform<T>(w.w[1]);
+        if (photon) {
+            ++c.v[C_EV];
+            pair_shares<T>(a.tab.nbw_inv, echi, r1, xa, xb, oor);
+            ++c.v[C_PAIR];
+        } else if (e_aux < (T)0) {
+            ++c.v[C_EV];
+            xa = photon_s<T>(a.tab.nlc_inv, echi, r1, oor);      // s
+            xb = uniform<T>(w.w[0]);                               // for the fresh optical depth
+            ++c.v[C_EMIT];
+        } else {
+            // beyond-LCFA: LCFA sample, then the rejection of Eq. rej_cond below gamma_LCFA
+            xa = photon_s<T>(a.tab.nlc_inv, echi, r1, oor);
+            xb = (T)-1;                                            // marks: no optical depth
+            bool accept = true;
+            const T gbar = eg * xa / ((T)1 + xa);
+            if (e_aux > (T)0 && !(gbar > e_aux)) {
+                const T uL = e_aux / (eg - e_aux);
+                const T lhs = log(uniform<T>(w.w[2])) + ln_spectrum<T>(a.tab.k23, a.tab.ki13, xa, echi, oor);
+                const T rhs = ln_spectrum<T>(a.tab.k23, a.tab.ki13, uL, echi, oor);
+                accept = lhs <= rhs;
+            }
+            if (accept) {
+                ++c.v[C_EMIT];
+            } else {
+                nprod = 0;
+                ++c.v[C_REJ];
+            }
+        }
+        c.v[C_OOR] += oor;
+    }
+    if (late) reserve_records(a.ocount, a.scount, nprod, nspawn, bp, bs);
     if (!valid) return;
     const T pm = sqrt(fma(px, px, fma(py, py, pz * pz)));
     const T inv_pm = pm > (T)0 ? (T)1 / pm : (T)0;
     const T nx = px * inv_pm, ny = py * inv_pm, nz = pz * inv_pm;
     if (photon) {
         // pair creation: the photon is removed, two leptons along its direction
-        const T pme = lepton_pmag(xa * e.g, c), pmp = lepton_pmag(xb * e.g, c);
+        const T pme = lepton_pmag(xa * eg, c), pmp = lepton_pmag(xb * eg, c);
 #pragma unroll
         for (int m = 0; m < 2; ++m) {
             const unsigned long long j = bp + m;
@@ -336,20 +349,20 @@ __device__ __forceinline__ void process_events(const StepArgs<T> &a, const E &e,
 #pragma unroll
                         for (int d3 = 0; d3 < 3; ++d3) { a.sfp[d3][s] = (T)0; a.sdf[d3][s] = (T)0; }
                     }
-                    if (a.sk0) a.sk0[s] = a.k0[e.i];
-                    if (a.samp) a.samp[s] = a.amp ? a.amp[e.i] : a.amp0;
+                    if (a.sk0) a.sk0[s] = a.k0[ei];
+                    if (a.samp) a.samp[s] = a.amp ? a.amp[ei] : a.amp0;
                 } else {
                     ++c.v[C_SDROP];
                 }
             }
         }
-        a.flags[e.i] = (uint8_t)(fl & ~SFQ_ALIVE);
+        a.flags[ei] = (uint8_t)(fl & ~SFQ_ALIVE);
     } else if (nprod) {
         // photon emission: xi = s/(1+s) to the photon, the lepton keeps gamma/(1+s)
         const T s = xa;
         const T inv1s = (T)1 / ((T)1 + s);
-        const T gph = e.g * s * inv1s;
-        const T pnew = lepton_pmag(e.g * inv1s, c);
+        const T gph = eg * s * inv1s;
+        const T pnew = lepton_pmag(eg * inv1s, c);
         const unsigned long long j = bp;
         if (j < (unsigned long long)a.cap) {
             a.opx[j] = nx * gph; a.opy[j] = ny * gph; a.opz[j] = nz * gph;
@@ -359,11 +372,11 @@ __device__ __forceinline__ void process_events(const StepArgs<T> &a, const E &e,
         } else {
             ++c.v[C_DROP];
         }
-        a.px[e.i] = nx * pnew; a.py[e.i] = ny * pnew; a.pz[e.i] = nz * pnew;
-        if (xb > (T)0) a.tau[e.i] = to_tau<T>(fresh_tau(xb));   // fresh optical depth, word 0 (Sec. 2)
+        a.px[ei] = nx * pnew; a.py[ei] = ny * pnew; a.pz[ei] = nz * pnew;
+        if (xb > (T)0) a.tau[ei] = to_tau<T>(fresh_tau(xb));   // fresh optical depth, word 0 (Sec. 2)
         // a lepton left without momentum is outside the ultrarelativistic regime of the rates
         // and has no direction for collinear emission: it leaves the step
-        if (!(pnew > (T)0)) a.flags[e.i] = (uint8_t)(fl & ~SFQ_ALIVE);
+        if (!(pnew > (T)0)) a.flags[ei] = (uint8_t)(fl & ~SFQ_ALIVE);
     }
 }
 
@@ -496,15 +509,17 @@ __global__ void __launch_bounds__(STEP_BS, SFQ_STEP_MINB) mc_step_kernel(const S
             const QEntryX<T> e = q[(head + lane) & (QS - 1)];
             __syncwarp();
             head += 32;
-            process_events<T>(a, e, e.aux, true, c);
+            process_events<T>(a, e.i, e.g, e.chi, e.aux, a.px[e.i], a.py[e.i], a.pz[e.i], a.flags[e.i], true, c);
         }
     }
     // drain the partial batch
     __syncwarp();
     if (tail != head) {
         const unsigned nv = tail - head;
-        QEntryX<T> e = q[(head + lane) & (QS - 1)];
-        process_events<T>(a, e, e.aux, (unsigned)lane < nv, c);
+        const QEntryX<T> e = q[(head + lane) & (QS - 1)];
+        const bool v = (unsigned)lane < nv;
+        process_events<T>(a, e.i, e.g, e.chi, e.aux, v ? a.px[e.i] : (T)0, v ? a.py[e.i] : (T)0,
+                          v ? a.pz[e.i] : (T)0, v ? a.flags[e.i] : (uint8_t)0, v, c);
     }
     flush_counters(c, a.counters);
 }

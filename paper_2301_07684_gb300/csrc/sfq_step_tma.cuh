@@ -4,7 +4,8 @@
 // slices (momenta, optical depth, flags, fields or phase index) from global to
 // shared memory with 1D bulk copies (cp.async.bulk), NSTAGE tiles ahead, and 16
 // consumer warps compute the step (Sec. 2 and 4 of Montefiori & Tamburini,
-// arXiv:2301.07684) from shared memory.  Stages are handed over with mbarriers
+// arXiv:2301.07684) from shared memory.  Each consumer warp queues its event particles,
+// with the state it read, in a ring of its own and samples them 32 at a time.  Stages are handed over with mbarriers
 // (full: producer -> consumers, completed by the copies' transaction bytes;
 // empty: consumers -> producer).  Every wait is bounded: on a timeout the kernel
 // raises the timeout word of the counters and leaves its loops after its copies
@@ -14,7 +15,6 @@
 
 namespace sfq {
 
-constexpr int TMA_NSTAGE = 3;
 constexpr uint32_t TMA_WAIT_LIMIT = 1u << 24;   // try_wait polls before a wait is declared failed
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -66,9 +66,28 @@ struct TmaStage {
     static constexpr size_t BYTES = FK == FK_SOA ? O_F + NF * TILE * sizeof(T) : O_AMP + TILE * sizeof(T);
 };
 
+// Dynamic shared memory of one CTA: NSTAGE stages, then the consumer warps' event queues
+// (QS entries each: one tile's events plus a partial batch), then the mbarriers.  Three
+// stages where they fit beside the queues and the static rate tables, else two.
+template <typename T, int FK, int CW>
+struct TmaCfg {
+    using S = TmaStage<T, FK, CW>;
+    static constexpr int PPL = S::TILE / CW / 32;                  // particles per lane per tile
+    static constexpr int QS = 32 * (PPL + 1) <= 64 ? 64 : (32 * (PPL + 1) <= 128 ? 128 : 256);
+    static constexpr size_t QBYTES = (size_t)CW * QS * sizeof(QEntry<T>);
+    static constexpr size_t STATIC = (RateSmem<T>::NLC_N + RateSmem<T>::NBW_N) * sizeof(T);
+    static constexpr size_t LIMIT = 227 * 1024;                    // shared memory per CTA
+    static constexpr int NSTAGE = 3 * S::BYTES + QBYTES + STATIC + 1024 <= LIMIT ? 3 : 2;
+    static constexpr size_t O_Q = (size_t)NSTAGE * S::BYTES;
+    static constexpr size_t O_BAR = O_Q + QBYTES;
+    static constexpr size_t SMEM = O_BAR + 2 * NSTAGE * sizeof(uint64_t) + 64;
+    static_assert(S::BYTES % 16 == 0 && QBYTES % 16 == 0, "stage and queue offsets keep 16-byte alignment");
+    static_assert(SMEM + STATIC <= LIMIT, "shared memory of the TMA-staged step");
+};
+
 template <typename T, int FK, int CW>
 constexpr size_t tma_smem_bytes() {
-    return (size_t)TMA_NSTAGE * TmaStage<T, FK, CW>::BYTES + 2 * TMA_NSTAGE * sizeof(uint64_t) + 64;
+    return TmaCfg<T, FK, CW>::SMEM;
 }
 
 // A wait that gave up is recorded in the counters.
@@ -80,21 +99,23 @@ template <typename T, int FK, int CW>
 __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const StepArgs<T> a) {
     using Q = L<T>;
     using S = TmaStage<T, FK, CW>;
+    using CFG = TmaCfg<T, FK, CW>;
+    constexpr int TMA_NSTAGE = CFG::NSTAGE;
     constexpr int TMA_CONSUMER_WARPS = CW;
     constexpr int TMA_THREADS = 32 * (CW + 1);
     constexpr int TILE = S::TILE;
     constexpr int PER_WARP = TILE / TMA_CONSUMER_WARPS;    // particles per consumer warp per tile
-    constexpr int PPL = PER_WARP / 32;                     // particles per lane per tile
-    constexpr int QS = 32 * (PPL + 1) <= 64 ? 64 : (32 * (PPL + 1) <= 128 ? 128 : 256);  // one tile + a partial batch
+    constexpr int PPL = CFG::PPL;                          // particles per lane per tile
+    constexpr int QS = CFG::QS;                            // one tile + a partial batch
     constexpr bool PAIRED = sizeof(T) == 4 && PPL == 2;     // adjacent-pair vector layout
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + TMA_NSTAGE * S::BYTES);
+    QEntry<T> *wq = reinterpret_cast<QEntry<T> *>(smem + CFG::O_Q);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + CFG::O_BAR);
     uint64_t *empty = full + TMA_NSTAGE;
     int *abort_flag = reinterpret_cast<int *>(empty + TMA_NSTAGE);
     using RS = RateSmem<T>;
     __shared__ __align__(16) T s_nlc[RS::NLC_N];
     __shared__ __align__(16) T s_nbw[RS::NBW_N];
-    __shared__ QEntry<T> wq[TMA_CONSUMER_WARPS][QS];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     stage_rate_table<T, Q::NLC_DEG, RS::NLC_STRIDE>(s_nlc, a.tab.nlc_rate, Q::RATE_NLC_N / (Q::NLC_DEG + 1),
@@ -162,7 +183,7 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
     }
 
     // ------------------------------------------------------------------ consumers
-    QEntry<T> *q = wq[warp];
+    QEntry<T> *q = wq + (size_t)warp * QS;
     unsigned head = 0, tail = 0;
     Cnt c;
     c.zero();
@@ -184,7 +205,8 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
         const double *stau = reinterpret_cast<const double *>(st + S::O_TAU);
         const uint8_t *sfl = st + S::O_FL;
         bool ev[PPL];
-        T gk[PPL], ck[PPL];
+        T gk[PPL], ck[PPL], pk[PPL][3];
+        uint8_t fk[PPL];
         if (staged && PAIRED) {
             // full tile, binary32: lane takes the adjacent particles li0, li0 + 1 (vector loads)
             const int li0 = warp * PER_WARP + 2 * lane;
@@ -209,6 +231,10 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
                 ev[k] = false;
                 gk[k] = (T)0;
                 ck[k] = (T)0;
+                pk[k][0] = k == 0 ? vx.x : vx.y;
+                pk[k][1] = k == 0 ? vy.x : vy.y;
+                pk[k][2] = k == 0 ? vz.x : vz.y;
+                fk[k] = fl;
                 if (fl & SFQ_ALIVE) {
                     T E[3], B[3];
                     if (FK == FK_SOA) {
@@ -243,6 +269,10 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
                 ev[k] = false;
                 gk[k] = (T)0;
                 ck[k] = (T)0;
+                pk[k][0] = spx[li];
+                pk[k][1] = spy[li];
+                pk[k][2] = spz[li];
+                fk[k] = fl;
                 if (fl & SFQ_ALIVE) {
                     T E[3], B[3];
                     if (FK == FK_SOA) {
@@ -258,7 +288,7 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
                         E[0] = (T)0; E[1] = f; E[2] = (T)0;
                         B[0] = (T)0; B[1] = (T)0; B[2] = f;
                     }
-                    ev[k] = step_particle<T>(a, s_nlc, s_nbw, start + li, fl, spx[li], spy[li], spz[li], E, B,
+                    ev[k] = step_particle<T>(a, s_nlc, s_nbw, start + li, fl, pk[k][0], pk[k][1], pk[k][2], E, B,
                                              stau[li], gk[k], ck[k], c);
                 }
             }
@@ -271,12 +301,16 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
                 ev[k] = false;
                 gk[k] = (T)0;
                 ck[k] = (T)0;
+                pk[k][0] = pk[k][1] = pk[k][2] = (T)0;
+                fk[k] = 0;
                 if (i < n_eff) {
                     const uint8_t fl = a.flags[i];
+                    fk[k] = fl;
                     if (fl & SFQ_ALIVE) {
                         T E[3], B[3];
                         load_fields<T, FK>(a, i, E, B);
-                        ev[k] = step_particle<T>(a, s_nlc, s_nbw, i, fl, a.px[i], a.py[i], a.pz[i], E, B, a.tau[i],
+                        pk[k][0] = a.px[i]; pk[k][1] = a.py[i]; pk[k][2] = a.pz[i];
+                        ev[k] = step_particle<T>(a, s_nlc, s_nbw, i, fl, pk[k][0], pk[k][1], pk[k][2], E, B, a.tau[i],
                                                  gk[k], ck[k], c);
                     }
                 }
@@ -292,6 +326,10 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
                                          : start + warp * PER_WARP + k * 32 + lane;
                 e.g = gk[k];
                 e.chi = ck[k];
+                e.px = pk[k][0];
+                e.py = pk[k][1];
+                e.pz = pk[k][2];
+                e.fl = fk[k];
                 q[(tail + r) & (QS - 1)] = e;
             }
             tail += __popc(m);
@@ -302,14 +340,14 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
             const QEntry<T> e = q[(head + lane) & (QS - 1)];
             __syncwarp();
             head += 32;
-            process_events<T>(a, e, (T)-1, true, c);
+            process_events<T>(a, e.i, e.g, e.chi, (T)-1, e.px, e.py, e.pz, (uint8_t)e.fl, true, c);
         }
     }
     __syncwarp();
     if (tail != head) {
         const unsigned nv = tail - head;
-        QEntry<T> e = q[(head + lane) & (QS - 1)];
-        process_events<T>(a, e, (T)-1, (unsigned)lane < nv, c);
+        const QEntry<T> e = q[(head + lane) & (QS - 1)];
+        process_events<T>(a, e.i, e.g, e.chi, (T)-1, e.px, e.py, e.pz, (uint8_t)e.fl, (unsigned)lane < nv, c);
     }
     // counters of the consumer warps (the producer warp has returned)
     if (a.counters) {
