@@ -378,7 +378,50 @@ def run_ours(args):
         torch.cuda.empty_cache()
         return out_s
 
+    def fused_leg(precision):
+        """The config-2 workload with the analytic plane wave, all timed steps in one launch of
+        the fused kernel (each particle's state in registers across the steps)."""
+        dtype = torch.float32 if precision == "fp32" else torch.float64
+        ctx = sfq.Context(ref_len_m=W.REF_LEN, dt=W.DT, precision=precision, seed=12345, device=local)
+        P = make_state(sfq, torch, d, dtype, device)
+        P.id_base = rank * n
+        table = torch.as_tensor(d["table"]).to(device=device, dtype=dtype)
+        k0 = torch.as_tensor(d["k0"].view(np.int32)).to(device)
+        F = sfq.FieldSource.plane_wave(k0, table, d["k_step"], amp0=d["amp0"])
+        steps, warm = args.steps, args.warmup
+        out = sfq.ProductBuffers(int(0.09 * n * (steps + 1)) + 4096, dtype, device)
+        cnt = sfq.counters_tensor(device)
+        ctx.mc_run_fused(P, F, 0, warm, out, counters=cnt)            # warm-up steps
+        out.reset()
+        cnt.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        e0.record()
+        ctx.mc_run_fused(P, F, warm, steps, out, counters=cnt)
+        e1.record()
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1)
+        c = sfq.counters_dict(cnt)
+        esz = 4 if precision == "fp32" else 8
+        # the population is read and written once per launch; every record is written
+        state_bytes = n * ((3 * esz + 8 + 1 + 4) + (3 * esz + 8 + 1))
+        rec_bytes = c["emitted"] * (3 * esz + 8 + 4 + 1)
+        res = {"value": n * steps / (ms * 1e-3), "unit": UNIT, "ms": ms, "ms_per_step": ms / steps,
+               "steps_per_launch": steps, "launches": 1, "precision": precision,
+               "bytes_per_update": (state_bytes + rec_bytes) / (n * steps),
+               "events_per_update": c["events"] / (n * steps), "dropped": c["dropped"], "clocks": clk,
+               "bound": "issue (per-update arithmetic and event sampling; HBM traffic ~2 B/update)"}
+        ctx.close()
+        del P, out
+        torch.cuda.empty_cache()
+        return res
+
     main = one_path("fp32", "soa", args.steps, args.warmup, with_e2e=True)
+    fused = fused_leg("fp32") if args.fused else None
+    fused64 = fused_leg("fp64") if args.fused else None
     pw = one_path("fp32", "pw", args.steps, args.warmup, with_e2e=False)
     f64_steps = max(2, args.steps // 10)
     f64 = one_path("fp64", "soa", f64_steps, max(3, min(args.warmup, 3)), with_e2e=False)
@@ -420,6 +463,8 @@ def run_ours(args):
             "plane_wave_fields": {"value": pw["value"], "unit": UNIT, "ms_per_step": pw["ms_per_step"],
                                   "achieved_gbs": pw["achieved_gbs"], "frac": pw["frac"],
                                   "bytes_per_update": pw["bytes_per_update"]},
+            "fused_plane_wave": fused,
+            "fused_plane_wave_fp64": fused64,
             "batched": batched,
             "surrogate": surrogate,
             "events_per_update": main["events_per_update"],
@@ -497,6 +542,7 @@ def main():
                     help="scale of the 64-beam particle counts")
     ap.add_argument("--surrogate-steps", type=int, default=30000,
                     help="training steps of the surrogate leg (0 skips it)")
+    ap.add_argument("--fused", type=int, default=1, help="time the fused multi-step plane-wave run (0: skip)")
     ap.add_argument("--oracle-particles", type=int, default=512)
     ap.add_argument("--oracle-steps", type=int, default=50)
     # DRAM bytes (read + write) per update of mc_step_tma_kernel<float, SoA, 16 warps>, from the

@@ -229,6 +229,24 @@ sfq_status sfq_mc_run(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f,
                       const sfq_fields *children_fields, uint32_t step0, uint32_t nsteps, const sfq_products *out,
                       const sfq_spawn *spawn, sfq_counters *counters, void *stream);
 
+/* Steps step0 ... step0+nsteps-1 of `p` in the analytic plane-wave field, fused into one
+ * launch: each particle is loaded once, stepped nsteps times with its momentum, optical
+ * depth, flags and phase held in registers, and stored once, so the run reads and writes
+ * the population once instead of once per step.  Per update and per event it performs
+ * exactly the arithmetic of sfq_mc_step (Sec. 2 and 4: chi, rate, binary64 optical depth,
+ * Philox draws keyed by the particle's own step, energy sampling, recoil), so the product
+ * records (in another order), the final state and the counters equal those of sfq_mc_step
+ * called for step0, step0+1, ... in turn without children.
+ * Requirements (else SFQ_ERR_ARG): f->kind == SFQ_FIELDS_PLANE_WAVE with
+ * n_table <= SFQ_FUSED_TABLE_MAX; p->lepton_model == SFQ_LEPTON_LCFA_OD; step0 + nsteps
+ * < 2^32.  Photons that convert are removed and leave their two product records; their
+ * leptons are not stepped (no sfq_spawn).  Buffers and alignment as for sfq_mc_step;
+ * `out` must hold the records of all nsteps steps (records past its capacity are counted
+ * as dropped).  Asynchronous on `stream`. */
+#define SFQ_FUSED_TABLE_MAX 8192
+sfq_status sfq_mc_run_fused(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, uint32_t step0,
+                            uint32_t nsteps, const sfq_products *out, sfq_counters *counters, void *stream);
+
 /* Autotuner: times every launch shape of sfq_mc_step (kernel variant, particles per lane
  * or warps per block) on a copy of up to `sample_n` particles of `p` (the caller's state
  * is not modified; the copy lives in temporary device memory for the duration of the

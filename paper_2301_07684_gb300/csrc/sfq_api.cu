@@ -279,6 +279,24 @@ sfq_status sfq_mc_step(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f
     return e == cudaSuccess ? SFQ_OK : cuda_fail(ctx, e, "sfq_mc_step");
 }
 
+sfq_status sfq_mc_run_fused(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, uint32_t step0,
+                            uint32_t nsteps, const sfq_products *out, sfq_counters *counters, void *stream) {
+    if (!ctx) return SFQ_ERR_ARG;
+    const sfq_status st = sfq::validate_step(ctx, p, f, out, nullptr, counters);
+    if (st != SFQ_OK) return st;
+    if (f->kind != SFQ_FIELDS_PLANE_WAVE) return fail(ctx, SFQ_ERR_ARG, "fused run: plane-wave fields only");
+    if (p->lepton_model != SFQ_LEPTON_LCFA_OD) return fail(ctx, SFQ_ERR_ARG, "fused run: optical-depth leptons only");
+    if (f->n_table > (uint32_t)SFQ_FUSED_TABLE_MAX)
+        return fail(ctx, SFQ_ERR_ARG, "fused run: cosine table longer than SFQ_FUSED_TABLE_MAX");
+    if ((uint64_t)step0 + nsteps > 0xFFFFFFFFull) return fail(ctx, SFQ_ERR_ARG, "step0 + nsteps exceeds 2^32 - 1");
+    if (p->n == 0 || nsteps == 0) return SFQ_OK;
+    DeviceGuard g(ctx->device);
+    sfq::StepLaunch L{ctx, p, f, step0, out, nullptr, counters, (cudaStream_t)stream, 0, 0, 0};
+    const cudaError_t e = ctx->cfg.precision == SFQ_FP64 ? sfq::launch_fused_f64(L, nsteps)
+                                                         : sfq::launch_fused_f32(L, nsteps);
+    return e == cudaSuccess ? SFQ_OK : cuda_fail(ctx, e, "sfq_mc_run_fused");
+}
+
 sfq_status sfq_set_step_shape(sfq_ctx *ctx, int32_t variant, int32_t ppt, int32_t grid_blocks) {
     if (!ctx) return SFQ_ERR_ARG;
     if (variant < 0 || variant > 2) return fail(ctx, SFQ_ERR_ARG, "variant must be 0, 1 or 2");

@@ -69,6 +69,8 @@ cudaError_t launch_uniforms_f64(int64_t n, const uint64_t *id, uint32_t step, ui
                                 void *u, cudaStream_t s, int grid);
 cudaError_t launch_step_f32(const StepLaunch &);
 cudaError_t launch_step_f64(const StepLaunch &);
+cudaError_t launch_fused_f32(const StepLaunch &, uint32_t nsteps);
+cudaError_t launch_fused_f64(const StepLaunch &, uint32_t nsteps);
 
 sfq_status validate_step(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, const sfq_products *out,
                          const sfq_spawn *spawn, const sfq_counters *counters);

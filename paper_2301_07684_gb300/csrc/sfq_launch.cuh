@@ -2,6 +2,7 @@
 // sfq_launch_f64.cu with SFQ_T set to float or double.
 #pragma once
 #include "sfq_internal.h"
+#include "sfq_fused.cuh"
 #include "sfq_step_tma.cuh"
 
 namespace sfq {
@@ -74,12 +75,12 @@ static cudaError_t prepare_step_t() {
     return e;
 }
 
+// Kernel arguments of one step (or of the first step of a fused run) from the C descriptors.
 template <typename T>
-static cudaError_t launch_step_t(const StepLaunch &L) {
+static StepArgs<T> make_step_args(const StepLaunch &L) {
     const sfq_particles &p = *L.p;
     const sfq_fields &f = *L.f;
     const sfq_ctx *ctx = L.ctx;
-    if (p.n == 0) return cudaSuccess;
     StepArgs<T> a{};
     a.n = p.n;
     a.n_dev = p.n_dev;
@@ -133,6 +134,16 @@ static cudaError_t launch_step_t(const StepLaunch &L) {
     a.inv_dt2 = (T)(1.0 / (ctx->cfg.dt * ctx->cfg.dt));
     a.tab = tables_of<T>(ctx);
     a.counters = L.counters;
+    return a;
+}
+
+template <typename T>
+static cudaError_t launch_step_t(const StepLaunch &L) {
+    const sfq_particles &p = *L.p;
+    const sfq_fields &f = *L.f;
+    const sfq_ctx *ctx = L.ctx;
+    if (p.n == 0) return cudaSuccess;
+    const StepArgs<T> a = make_step_args<T>(L);
     const bool pw = f.kind == SFQ_FIELDS_PLANE_WAVE;
     // TMA-staged kernel: one persistent block per SM; chosen automatically when every
     // SM gets at least one full tile.  `ppt` selects the consumer warps per block.
@@ -186,6 +197,38 @@ static cudaError_t launch_step_t(const StepLaunch &L) {
         if (need < grid) grid = (int)(need > 0 ? need : 1);
     }
     kern<<<grid, STEP_BS, 0, L.stream>>>(a);
+    return cudaGetLastError();
+}
+
+// nsteps steps from L.step on in one launch of the fused plane-wave kernel (sfq_fused.cuh).
+template <typename T>
+static cudaError_t launch_fused_t(const StepLaunch &L, uint32_t nsteps) {
+    constexpr int PPL = sizeof(T) == 4 ? 4 : 2;
+    using CFG = FusedCfg<T, PPL>;
+    const sfq_particles &p = *L.p;
+    const sfq_fields &f = *L.f;
+    if (p.n == 0 || nsteps == 0) return cudaSuccess;
+    const StepArgs<T> a = make_step_args<T>(L);
+    auto kern = mc_fused_kernel<T, PPL>;
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)CFG::smem(FUSED_TABLE_MAX));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const size_t smem = CFG::smem(f.n_table);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FUSED_BS, smem);
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+    int grid = L.grid > 0 ? L.grid : per_sm * L.ctx->num_sms;
+    const int64_t chunks = (p.n + 32 * PPL - 1) / (32 * PPL);
+    const int64_t need = (chunks + CFG::WARPS - 1) / CFG::WARPS;
+    if (need < grid) grid = (int)need;
+    const uint32_t K = f.n_table;
+    const uint32_t kstep = f.k_step % K;
+    const uint32_t off0 = (uint32_t)(((uint64_t)L.step * (uint64_t)f.k_step) % (uint64_t)K);
+    kern<<<grid, FUSED_BS, smem, L.stream>>>(a, L.step, nsteps, off0, kstep);
     return cudaGetLastError();
 }
 

@@ -10,4 +10,5 @@ cudaError_t launch_uniforms_f32(int64_t n, const uint64_t *id, uint32_t step, ui
 }
 cudaError_t launch_step_f32(const StepLaunch &L) { return launch_step_t<float>(L); }
 cudaError_t prepare_step_f32() { return prepare_step_t<float>(); }
+cudaError_t launch_fused_f32(const StepLaunch &L, uint32_t nsteps) { return launch_fused_t<float>(L, nsteps); }
 }  // namespace sfq

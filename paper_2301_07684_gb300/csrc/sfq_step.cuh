@@ -120,6 +120,21 @@ __device__ __forceinline__ T chi_of(T g, T px, T py, T pz, const T E[3], const T
     return sqrt_nr(q) * inv_rho;
 }
 
+// chi in the linearly polarised plane wave E = (0, f, 0), B = (0, 0, f): Eq. chi_exact with
+// the vanishing components dropped (gamma E + p x B = (py f, gamma f - px f, 0), p.E = py f).
+// Every operation is rounded explicitly, so all kernels form the same bits.
+__device__ __forceinline__ float mul_rn(float x, float y) { return __fmul_rn(x, y); }
+__device__ __forceinline__ double mul_rn(double x, double y) { return __dmul_rn(x, y); }
+__device__ __forceinline__ float sub_rn(float x, float y) { return __fsub_rn(x, y); }
+__device__ __forceinline__ double sub_rn(double x, double y) { return __dsub_rn(x, y); }
+template <typename T>
+__device__ __forceinline__ T chi_pw(T g, T px, T py, T f, T inv_rho) {
+    const T fx = mul_rn(py, f);
+    const T fy = fma(g, f, -mul_rn(px, f));
+    const T q = sub_rn(fma(fx, fx, mul_rn(fy, fy)), mul_rn(fx, fx));
+    return sqrt_nr(q) * inv_rho;
+}
+
 // Optical-depth decrement (Sec. 2).  Returns true on an event; otherwise stores
 // the new tau.  `draw0` holds -ln(u3) when the particle arrived without one.
 template <typename IdF>
@@ -136,7 +151,9 @@ __device__ __forceinline__ bool od_update(double *tau_ptr, float d, uint64_t see
     const uint32_t db = __float_as_uint(d);
     const uint64_t dd = ((db >> 23) - 1u < 254u) ? f32_to_f64_bits(d) : 0ull;   // normal d > 0, else 0
     const double t = __dsub_rn(__longlong_as_double((long long)b), __longlong_as_double((long long)dd));
-    if (t < 0.0) return true;
+    // the difference of two non-negative binary64 values is negative exactly when its sign
+    // bit is set (it is never -0), so the test runs on the integer pipe
+    if (__double_as_longlong(t) < 0) return true;
     *tau_ptr = t;
     return false;
 }
@@ -149,7 +166,7 @@ __device__ __forceinline__ bool od_update(double *tau_ptr, double d, uint64_t se
         t = -log(uniform<double>(w.w[3]));
     }
     t = t - d;
-    if (t < 0.0) return true;
+    if (__double_as_longlong(t) < 0) return true;   // t < 0 (never -0: tau, d >= 0)
     *tau_ptr = t;
     return false;
 }
@@ -236,6 +253,16 @@ __device__ __forceinline__ bool blcfa_phase_a(const StepArgs<T> &a, const T *s_n
     return true;
 }
 
+// New state of an event's parent, returned by process_events_core: bit 0 of `what` =
+// momentum replaced, bit 1 = fresh optical depth, bit 2 = flags replaced.
+template <typename T>
+struct EvOut {
+    T px, py, pz;
+    double tau;
+    uint8_t fl;
+    uint8_t what;
+};
+
 // Warp-collective reservation of nprod product records and nspawn children per lane:
 // one atomic per counter for the warp; returns each lane's first index.
 __device__ __forceinline__ void reserve_records(unsigned long long *ocount, unsigned long long *scount, int nprod,
@@ -268,8 +295,10 @@ __device__ __forceinline__ void reserve_records(unsigned long long *ocount, unsi
 // front (no beyond-LCFA lane, whose emission may be rejected), so that the atomic's
 // latency overlaps the sampling.
 template <typename T>
-__device__ __forceinline__ void process_events(const StepArgs<T> &a, int64_t ei, T eg, T echi, T e_aux, T px,
-                                               T py, T pz, uint8_t fl, bool valid, Cnt &c) {
+__device__ __forceinline__ void process_events_core(const StepArgs<T> &a, uint32_t step, int64_t ei, T eg, T echi,
+                                                    T e_aux, T px, T py, T pz, uint8_t fl, bool valid, Cnt &c,
+                                                    EvOut<T> &o) {
+    o.what = 0;
     const bool photon = valid && ((fl >> SFQ_SPECIES_SHIFT) & 3) == SFQ_PHOTON;
     const bool maybe = valid && !photon && !(e_aux < (T)0);        // beyond-LCFA: may be rejected
     const bool late = __any_sync(0xFFFFFFFFu, maybe);
@@ -284,7 +313,7 @@ __device__ __forceinline__ void process_events(const StepArgs<T> &a, int64_t ei,
     if (valid) {
         id = a.id ? a.id[ei] : a.id_base + (uint64_t)ei;
         tag = (fl >> SFQ_TAG_SHIFT) & 3u;
-        const u4 w = draws(a.seed, id, a.step, tag);
+        const u4 w = draws(a.seed, id, step, tag);
         const T r1 = uniform<T>(w.w[1]);
         if (photon) {
             ++c.v[C_EV];
@@ -331,7 +360,7 @@ __device__ __forceinline__ void process_events(const StepArgs<T> &a, int64_t ei,
             if (j < (unsigned long long)a.cap) {
                 a.opx[j] = nx * pmag; a.opy[j] = ny * pmag; a.opz[j] = nz * pmag;
                 a.opid[j] = id;
-                a.ostep[j] = a.step;
+                a.ostep[j] = step;
                 a.ometa[j] = (uint8_t)((m == 0 ? SFQ_ELECTRON : SFQ_POSITRON) | ((m + 1) << 2) | (tag << 4));
             } else {
                 ++c.v[C_DROP];
@@ -356,7 +385,8 @@ __device__ __forceinline__ void process_events(const StepArgs<T> &a, int64_t ei,
                 }
             }
         }
-        a.flags[ei] = (uint8_t)(fl & ~SFQ_ALIVE);
+        o.fl = (uint8_t)(fl & ~SFQ_ALIVE);
+        o.what = 4;
     } else if (nprod) {
         // photon emission: xi = s/(1+s) to the photon, the lepton keeps gamma/(1+s)
         const T s = xa;
@@ -367,23 +397,42 @@ __device__ __forceinline__ void process_events(const StepArgs<T> &a, int64_t ei,
         if (j < (unsigned long long)a.cap) {
             a.opx[j] = nx * gph; a.opy[j] = ny * gph; a.opz[j] = nz * gph;
             a.opid[j] = id;
-            a.ostep[j] = a.step;
+            a.ostep[j] = step;
             a.ometa[j] = (uint8_t)(SFQ_PHOTON | (tag << 4));
         } else {
             ++c.v[C_DROP];
         }
-        a.px[ei] = nx * pnew; a.py[ei] = ny * pnew; a.pz[ei] = nz * pnew;
-        if (xb > (T)0) a.tau[ei] = to_tau<T>(fresh_tau(xb));   // fresh optical depth, word 0 (Sec. 2)
+        o.px = nx * pnew; o.py = ny * pnew; o.pz = nz * pnew;
+        o.what = 1;
+        if (xb > (T)0) {                                        // fresh optical depth, word 0 (Sec. 2)
+            o.tau = to_tau<T>(fresh_tau(xb));
+            o.what |= 2;
+        }
         // a lepton left without momentum is outside the ultrarelativistic regime of the rates
         // and has no direction for collinear emission: it leaves the step
-        if (!(pnew > (T)0)) a.flags[ei] = (uint8_t)(fl & ~SFQ_ALIVE);
+        if (!(pnew > (T)0)) {
+            o.fl = (uint8_t)(fl & ~SFQ_ALIVE);
+            o.what |= 4;
+        }
     }
+}
+
+// process_events_core at the launch's step with the parent's new state stored to the
+// population in global memory.
+template <typename T>
+__device__ __forceinline__ void process_events(const StepArgs<T> &a, int64_t ei, T eg, T echi, T e_aux, T px,
+                                               T py, T pz, uint8_t fl, bool valid, Cnt &c) {
+    EvOut<T> o;
+    process_events_core<T>(a, a.step, ei, eg, echi, e_aux, px, py, pz, fl, valid, c, o);
+    if (o.what & 1) { a.px[ei] = o.px; a.py[ei] = o.py; a.pz[ei] = o.pz; }
+    if (o.what & 2) a.tau[ei] = o.tau;
+    if (o.what & 4) a.flags[ei] = o.fl;
 }
 
 // Per-lane computation of the rate and the optical-depth test for one particle held
 // in registers; returns true on an event (tau is then left to the event path).  Every
 // kernel shape calls this one routine, so results do not depend on the launch shape.
-template <typename T>
+template <typename T, bool PW = false>
 __device__ __forceinline__ bool step_particle(const StepArgs<T> &a, const T *s_nlc, const T *s_nbw, int64_t i,
                                               uint8_t fl, T px, T py, T pz, const T E[3], const T B[3],
                                               double tau_in, T &g, T &chi, Cnt &c) {
@@ -393,7 +442,7 @@ __device__ __forceinline__ bool step_particle(const StepArgs<T> &a, const T *s_n
     const T g2 = photon ? p2 : (T)1 + p2;
     const T inv_g = g2 > (T)0 ? rsqrt_nr(g2) : (T)0;
     g = sqrt_nr(g2);
-    chi = chi_of<T>(g, px, py, pz, E, B, a.inv_rho);
+    chi = PW ? chi_pw<T>(g, px, py, E[1], a.inv_rho) : chi_of<T>(g, px, py, pz, E, B, a.inv_rho);
     ++c.v[C_UPD];
     bool oor = false;
     T d;
@@ -415,16 +464,16 @@ __device__ __forceinline__ bool step_particle(const StepArgs<T> &a, const T *s_n
 }
 
 // As step_particle, with the optical depth passed in and out (stored by the caller).
-template <typename T>
+template <typename T, bool PW = false>
 __device__ __forceinline__ bool step_particle_v(const StepArgs<T> &a, const T *s_nlc, const T *s_nbw, int64_t i,
                                                 uint8_t fl, T px, T py, T pz, const T E[3], const T B[3],
-                                                double &tau, T &g, T &chi, Cnt &c) {
+                                                double &tau, T &g, T &chi, Cnt &c, uint32_t step) {
     const bool photon = ((fl >> SFQ_SPECIES_SHIFT) & 3) == SFQ_PHOTON;
     const T p2 = fma(px, px, fma(py, py, pz * pz));
     const T g2 = photon ? p2 : (T)1 + p2;
     const T inv_g = g2 > (T)0 ? rsqrt_nr(g2) : (T)0;
     g = sqrt_nr(g2);
-    chi = chi_of<T>(g, px, py, pz, E, B, a.inv_rho);
+    chi = PW ? chi_pw<T>(g, px, py, E[1], a.inv_rho) : chi_of<T>(g, px, py, pz, E, B, a.inv_rho);
     ++c.v[C_UPD];
     bool oor = false;
     T d;
@@ -439,7 +488,7 @@ __device__ __forceinline__ bool step_particle_v(const StepArgs<T> &a, const T *s
     c.v[C_OOR] += oor;
     c.v[C_RDT] += d > (T)0.1;
     const auto id_of = [&]() { return a.id ? a.id[i] : a.id_base + (uint64_t)i; };
-    return od_update(&tau, d, a.seed, id_of, a.step, (fl >> SFQ_TAG_SHIFT) & 3u);
+    return od_update(&tau, d, a.seed, id_of, step, (fl >> SFQ_TAG_SHIFT) & 3u);
 }
 
 // T: float (mixed) or double; FK: field source; PPT: particles per lane per chunk.
@@ -488,8 +537,8 @@ __global__ void __launch_bounds__(STEP_BS, SFQ_STEP_MINB) mc_step_kernel(const S
                 } else if (fl & SFQ_ALIVE) {
                     T E[3], B[3];
                     load_fields<T, FK>(a, i, E, B);
-                    ev = step_particle<T>(a, s_nlc, s_nbw, i, fl, a.px[i], a.py[i], a.pz[i], E, B, a.tau[i], g, chi,
-                                          c);
+                    ev = step_particle<T, FK == FK_PW>(a, s_nlc, s_nbw, i, fl, a.px[i], a.py[i], a.pz[i], E, B,
+                                                       a.tau[i], g, chi, c);
                 }
             }
             const unsigned m = __ballot_sync(0xFFFFFFFFu, ev);

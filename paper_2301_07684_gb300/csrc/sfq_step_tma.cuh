@@ -252,9 +252,9 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
                         E[0] = (T)0; E[1] = f; E[2] = (T)0;
                         B[0] = (T)0; B[1] = (T)0; B[2] = f;
                     }
-                    ev[k] = step_particle_v<T>(a, s_nlc, s_nbw, start + li0 + k, fl, k == 0 ? vx.x : vx.y,
+                    ev[k] = step_particle_v<T, FK == FK_PW>(a, s_nlc, s_nbw, start + li0 + k, fl, k == 0 ? vx.x : vx.y,
                                                k == 0 ? vy.x : vy.y, k == 0 ? vz.x : vz.y, E, B, tau_out[k],
-                                               gk[k], ck[k], c);
+                                               gk[k], ck[k], c, a.step);
                 }
             }
             // both optical depths in one 16-byte store (an event particle's value is
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
                         E[0] = (T)0; E[1] = f; E[2] = (T)0;
                         B[0] = (T)0; B[1] = (T)0; B[2] = f;
                     }
-                    ev[k] = step_particle<T>(a, s_nlc, s_nbw, start + li, fl, pk[k][0], pk[k][1], pk[k][2], E, B,
+                    ev[k] = step_particle<T, FK == FK_PW>(a, s_nlc, s_nbw, start + li, fl, pk[k][0], pk[k][1], pk[k][2], E, B,
                                              stau[li], gk[k], ck[k], c);
                 }
             }
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
                         T E[3], B[3];
                         load_fields<T, FK>(a, i, E, B);
                         pk[k][0] = a.px[i]; pk[k][1] = a.py[i]; pk[k][2] = a.pz[i];
-                        ev[k] = step_particle<T>(a, s_nlc, s_nbw, i, fl, pk[k][0], pk[k][1], pk[k][2], E, B, a.tau[i],
+                        ev[k] = step_particle<T, FK == FK_PW>(a, s_nlc, s_nbw, i, fl, pk[k][0], pk[k][1], pk[k][2], E, B, a.tau[i],
                                                  gk[k], ck[k], c);
                     }
                 }

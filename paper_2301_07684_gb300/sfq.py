@@ -90,6 +90,9 @@ def lib():
         L.sfq_mc_run.argtypes = [vp, C.POINTER(Particles), C.POINTER(Fields), C.POINTER(Particles),
                                  C.POINTER(Fields), u32, u32, C.POINTER(Products), C.POINTER(Spawn), vp, vp]
         L.sfq_mc_run.restype = st
+        L.sfq_mc_run_fused.argtypes = [vp, C.POINTER(Particles), C.POINTER(Fields), C.c_uint32, C.c_uint32,
+                                       C.POINTER(Products), vp, vp]
+        L.sfq_mc_run_fused.restype = st
         L.sfq_autotune_step.argtypes = [vp, C.POINTER(Particles), C.POINTER(Fields), u32, i64,
                                         C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_double), vp]
         L.sfq_autotune_step.restype = st
@@ -128,7 +131,7 @@ def lib():
 
 EXPORTED = ["sfq_init", "sfq_finalize", "sfq_last_error", "sfq_constants", "sfq_photon_rate", "sfq_pair_rate",
             "sfq_uniforms", "sfq_sample_photon_xi", "sfq_sample_pair_xi", "sfq_mc_step", "sfq_mc_run",
-            "sfq_autotune_step", "sfq_sort_scratch_bytes", "sfq_sort_products", "sfq_sort_products_noalloc", "sfq_set_step_shape",
+            "sfq_mc_run_fused", "sfq_autotune_step", "sfq_sort_scratch_bytes", "sfq_sort_products", "sfq_sort_products_noalloc", "sfq_set_step_shape",
             "sfq_mlp_num_params", "sfq_mlp_create", "sfq_mlp_destroy", "sfq_mlp_get_params", "sfq_mlp_set_params",
             "sfq_mlp_loss_grad", "sfq_mlp_train", "sfq_mlp_predict_lnw", "sfq_mlp_plain_targets", "sfq_mlp_calibrate",
             "sfq_mlp_sample_photon_xi",
@@ -261,6 +264,13 @@ class Context:
         ref = lambda x: C.byref(x) if x is not None else None
         self._check(lib().sfq_mc_run(self._h, C.byref(P), C.byref(F), ref(Cp), ref(Cf), step0, nsteps, C.byref(O),
                                      ref(S), _ptr(counters), _stream()), "sfq_mc_run")
+
+    def mc_run_fused(self, particles: "ParticleBuffers", fields: "FieldSource", step0: int, nsteps: int,
+                     products: "ProductBuffers", counters=None):
+        """nsteps steps in one launch of the fused plane-wave kernel (no children)."""
+        P, F, O = particles.descriptor(), fields.descriptor(), products.descriptor()
+        self._check(lib().sfq_mc_run_fused(self._h, C.byref(P), C.byref(F), step0, nsteps, C.byref(O),
+                                           _ptr(counters), _stream()), "sfq_mc_run_fused")
 
     def autotune_step(self, particles: "ParticleBuffers", fields: "FieldSource", step=0, sample_n=0):
         """Times every launch shape on a copy of the population; returns (variant, shape, ms)."""
