@@ -193,7 +193,12 @@ def run_ours(args):
             F = sfq.FieldSource.plane_wave(k0, table, d["k_step"], amp0=d["amp0"])
             fs = lambda s: F
         # launch shape from the autotuner (timed on a copy of the population)
-        tuned = ctx.autotune_step(P, fs(0), 0)
+        if args.shape:
+            v, sh = (int(x) for x in args.shape.split(":"))
+            ctx.set_step_shape(v, sh, 0)
+            tuned = (v, sh, None)
+        else:
+            tuned = ctx.autotune_step(P, fs(0), 0)
         clocks = ClockSampler(local)
         clocks.start()
         total_ms, launch_ms = time_mc(sfq, torch, ctx, P, fs, steps, warmup, out, cnt, n)
@@ -419,14 +424,15 @@ def run_ours(args):
         torch.cuda.empty_cache()
         return res
 
+    legs = set(args.legs.split(","))
     main = one_path("fp32", "soa", args.steps, args.warmup, with_e2e=True)
-    fused = fused_leg("fp32") if args.fused else None
-    fused64 = fused_leg("fp64") if args.fused else None
-    pw = one_path("fp32", "pw", args.steps, args.warmup, with_e2e=False)
+    fused = fused_leg("fp32") if "fused" in legs and args.fused else None
+    fused64 = fused_leg("fp64") if "fused64" in legs and args.fused else None
+    pw = one_path("fp32", "pw", args.steps, args.warmup, with_e2e=False) if "pw" in legs else None
     f64_steps = max(2, args.steps // 10)
-    f64 = one_path("fp64", "soa", f64_steps, max(3, min(args.warmup, 3)), with_e2e=False)
-    batched = batched_leg() if args.batched_steps > 0 else None
-    surrogate = surrogate_leg() if args.surrogate_steps > 0 else None
+    f64 = one_path("fp64", "soa", f64_steps, max(3, min(args.warmup, 3)), with_e2e=False) if "fp64" in legs else None
+    batched = batched_leg() if "batched" in legs and args.batched_steps > 0 else None
+    surrogate = surrogate_leg() if "surrogate" in legs and args.surrogate_steps > 0 else None
 
     # max over ranks of the headline time
     t = torch.tensor([main["ms_per_step"]], device=device)
@@ -457,10 +463,10 @@ def run_ours(args):
             "e2e": main["e2e"],
             "gpu_launches": args.steps,
             "clocks": main["clocks"],
-            "fp64_path": {"value": f64["value"], "unit": UNIT, "ms_per_step": f64["ms_per_step"],
+            "fp64_path": None if f64 is None else {"value": f64["value"], "unit": UNIT, "ms_per_step": f64["ms_per_step"],
                           "achieved_gbs": f64["achieved_gbs"], "hbm_frac": f64["frac"],
                           "steps": f64["steps"], "bound": "alu (fp64 pipe)"},
-            "plane_wave_fields": {"value": pw["value"], "unit": UNIT, "ms_per_step": pw["ms_per_step"],
+            "plane_wave_fields": None if pw is None else {"value": pw["value"], "unit": UNIT, "ms_per_step": pw["ms_per_step"],
                                   "achieved_gbs": pw["achieved_gbs"], "frac": pw["frac"],
                                   "bytes_per_update": pw["bytes_per_update"]},
             "fused_plane_wave": fused,
@@ -543,13 +549,17 @@ def main():
     ap.add_argument("--surrogate-steps", type=int, default=30000,
                     help="training steps of the surrogate leg (0 skips it)")
     ap.add_argument("--fused", type=int, default=1, help="time the fused multi-step plane-wave run (0: skip)")
+    ap.add_argument("--legs", default="pw,fp64,fused,fused64,batched,surrogate",
+                    help="legs timed beside the headline step (comma list; the headline always runs)")
+    ap.add_argument("--shape", default="",
+                    help="fixed launch shape 'variant:shape' of the per-step legs (e.g. 2:16) instead of the autotuner")
     ap.add_argument("--oracle-particles", type=int, default=512)
     ap.add_argument("--oracle-steps", type=int, default=50)
     # DRAM bytes (read + write) per update of mc_step_tma_kernel<float, SoA, 16 warps>, from the
     # ncu capture summarised in profiles/mc_step_tma_fp32_soa_4M.md (4,194,304 particles;
     # the per-particle streams scale in proportion to n).  Re-measure whenever that kernel
     # changes, and pass --traffic-per-update 0 to report null meanwhile.
-    ap.add_argument("--traffic-per-update", type=float, default=52.51,
+    ap.add_argument("--traffic-per-update", type=float, default=51.49,
                     help="DRAM bytes per update of the step kernel from an ncu capture (for roofline.traffic)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

@@ -272,11 +272,14 @@ __device__ __forceinline__ uint64_t fixed_to_tau(uint64_t u) {
     return (be << 52) | (m & 0xFFFFFFFFFFFFFull);
 }
 
-// binary32 -> binary64 bits for a finite positive normal value (exact).
+// binary32 -> binary64 bits for a finite positive normal value (exact), on 32-bit halves:
+// the high word is the binary32 pattern shifted right by 3 with the exponent rebiased by
+// 1023 - 127 = 896; the low word holds the last 3 mantissa bits.
 __device__ __forceinline__ uint64_t f32_to_f64_bits(float v) {
     const uint32_t b = __float_as_uint(v);
-    const uint64_t e = (uint64_t)((b >> 23) & 0xFFu) - 127 + 1023;
-    return (e << 52) | ((uint64_t)(b & 0x7FFFFFu) << 29);
+    const uint32_t hi = (b >> 3) + (896u << 20);
+    const uint32_t lo = b << 29;
+    return ((uint64_t)hi << 32) | lo;
 }
 
 }  // namespace sfq

@@ -441,7 +441,7 @@ __device__ __forceinline__ bool step_particle(const StepArgs<T> &a, const T *s_n
     // gamma and 1/gamma from one reciprocal square root
     const T g2 = photon ? p2 : (T)1 + p2;
     const T inv_g = g2 > (T)0 ? rsqrt_nr(g2) : (T)0;
-    g = sqrt_nr(g2);
+    g = g2 * inv_g;                                  // sqrt(g2) from the same reciprocal square root
     chi = PW ? chi_pw<T>(g, px, py, E[1], a.inv_rho) : chi_of<T>(g, px, py, pz, E, B, a.inv_rho);
     ++c.v[C_UPD];
     bool oor = false;
@@ -472,7 +472,7 @@ __device__ __forceinline__ bool step_particle_v(const StepArgs<T> &a, const T *s
     const T p2 = fma(px, px, fma(py, py, pz * pz));
     const T g2 = photon ? p2 : (T)1 + p2;
     const T inv_g = g2 > (T)0 ? rsqrt_nr(g2) : (T)0;
-    g = sqrt_nr(g2);
+    g = g2 * inv_g;                                  // sqrt(g2) from the same reciprocal square root
     chi = PW ? chi_pw<T>(g, px, py, E[1], a.inv_rho) : chi_of<T>(g, px, py, pz, E, B, a.inv_rho);
     ++c.v[C_UPD];
     bool oor = false;
