@@ -175,9 +175,11 @@ def run_ours(args):
     res = {}
     ids = None
 
-    def one_path(precision, fields_kind, steps, warmup, with_e2e):
+    def one_path(precision, fields_kind, steps, warmup, with_e2e, sampler_k=None):
         dtype = torch.float32 if precision == "fp32" else torch.float64
         ctx = sfq.Context(ref_len_m=W.REF_LEN, dt=W.DT, precision=precision, seed=12345, device=local)
+        if sampler_k:
+            ctx.set_sampler_coefficients(sampler_k)
         P = make_state(sfq, torch, d, dtype, device)
         P.id_base = rank * n
         nslab = steps + warmup
@@ -378,8 +380,38 @@ def run_ours(args):
                                      "plain_table_f32": 54027 * 4},
                  "bound": "alu (SFU: two exponential/reciprocal per SiLU, 192 SiLU per draw)"}
         net.close()
+        # the pair-creation surrogate: trained on the plain pair sampler's ln(-ln y), timed on
+        # 2^24 draws (chi log-uniform in [0.1, 100]) beside the plain pair sampler
+        pnet = sfq.Surrogate(ctx, seed=17, kind="pair")
+        chi_p = torch.as_tensor(np.exp(g.uniform(np.log(0.1), np.log(100.0), nt)).astype(np.float32)).to(device)
+        a_p = torch.as_tensor((np.abs(2.0 * ((g.integers(0, 1 << 23, nt) + 0.5) / (1 << 23)) - 1.0))
+                              .astype(np.float32)).to(device)
+        tgt = pnet.plain_targets(chi_p, a_p)
+        e0.record()
+        pnet.train(chi_p, a_p, tgt, steps=2 * steps_train, batch=8192, lr=3e-3, quantize=True, seed=19)
+        e1.record()
+        torch.cuda.synchronize()
+        ptrain_ms = e0.elapsed_time(e1)
+        pflag, perr = pnet.calibrate(3e-3)
+        npd = 1 << 24
+        chi_pd = torch.as_tensor(np.exp(g.uniform(np.log(0.1), np.log(100.0), npd)).astype(np.float32)).to(device)
+        r_pd = torch.as_tensor(((g.integers(0, 1 << 23, npd) + 0.5) / (1 << 23)).astype(np.float32)).to(device)
+        pcnt = sfq.counters_tensor(device)
+        t_pn = timed(lambda: pnet.sample_pair_xi(chi_pd, r_pd, use_flags=True, counters=pcnt))
+        t_pp = timed(lambda: ctx.sample_pair_xi(chi_pd, r_pd))
+        pc = sfq.counters_dict(pcnt)
+        out_s["pair"] = {"workload": "2^22 training pairs (targets from the plain pair sampler), 2^24 draws, "
+                                     "chi log-uniform in [0.1, 100]",
+                         "train_steps": 2 * steps_train, "train_ms": ptrain_ms, "calibration": {"tol_u": 3e-3, "flagged_cells": pflag,
+                                                                "max_unflagged_err_u": perr},
+                         "value": npd / (t_pn * 1e-3), "unit": "samples/s", "ms": t_pn,
+                         "fallback_fraction": pc["surrogate_fallbacks"] / (6 * npd),
+                         "plain_sampler": {"ms": t_pp, "samples_per_s": npd / (t_pp * 1e-3)},
+                         "footprint_bytes": {"network_bf16": sfq.Surrogate.num_params() * 2,
+                                             "plain_table_f32": 43092 * 4}}
+        pnet.close()
         ctx.close()
-        del chi_t, u_t, lnw_t, chi_d, u_d
+        del chi_t, u_t, lnw_t, chi_d, u_d, chi_p, a_p, tgt, chi_pd, r_pd
         torch.cuda.empty_cache()
         return out_s
 
@@ -431,6 +463,7 @@ def run_ours(args):
     pw = one_path("fp32", "pw", args.steps, args.warmup, with_e2e=False) if "pw" in legs else None
     f64_steps = max(2, args.steps // 10)
     f64 = one_path("fp64", "soa", f64_steps, max(3, min(args.warmup, 3)), with_e2e=False) if "fp64" in legs else None
+    trunc = one_path("fp32", "soa", args.steps, args.warmup, with_e2e=False, sampler_k=8) if "trunc" in legs else None
     batched = batched_leg() if "batched" in legs and args.batched_steps > 0 else None
     surrogate = surrogate_leg() if "surrogate" in legs and args.surrogate_steps > 0 else None
 
@@ -469,6 +502,10 @@ def run_ours(args):
             "plane_wave_fields": None if pw is None else {"value": pw["value"], "unit": UNIT, "ms_per_step": pw["ms_per_step"],
                                   "achieved_gbs": pw["achieved_gbs"], "frac": pw["frac"],
                                   "bytes_per_update": pw["bytes_per_update"]},
+            "sampler_8x8": None if trunc is None else {
+                "value": trunc["value"], "unit": UNIT, "ms_per_step": trunc["ms_per_step"], "frac": trunc["frac"],
+                "note": "headline workload with the inverse-CDF pieces cut to 8 x 8 Chebyshev coefficients "
+                        "(sfq_set_sampler_coefficients; worst w-bar error 6.3e-7)"},
             "fused_plane_wave": fused,
             "fused_plane_wave_fp64": fused64,
             "batched": batched,
@@ -549,7 +586,7 @@ def main():
     ap.add_argument("--surrogate-steps", type=int, default=30000,
                     help="training steps of the surrogate leg (0 skips it)")
     ap.add_argument("--fused", type=int, default=1, help="time the fused multi-step plane-wave run (0: skip)")
-    ap.add_argument("--legs", default="pw,fp64,fused,fused64,batched,surrogate",
+    ap.add_argument("--legs", default="pw,fp64,trunc,fused,fused64,batched,surrogate",
                     help="legs timed beside the headline step (comma list; the headline always runs)")
     ap.add_argument("--shape", default="",
                     help="fixed launch shape 'variant:shape' of the per-step legs (e.g. 2:16) instead of the autotuner")

@@ -247,6 +247,34 @@ sfq_status sfq_mc_run(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f,
 sfq_status sfq_mc_run_fused(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, uint32_t step0,
                             uint32_t nsteps, const sfq_products *out, sfq_counters *counters, void *stream);
 
+/* Options of a context.  Both are read when work is enqueued; a CUDA graph recorded by
+ * sfq_mc_run keeps the options it was recorded with, and a later call with other options
+ * records a new graph.
+ *
+ * Pair-rate cutoff: the NBW rate (sfq_pair_rate and the photon step) is zero below
+ * chi_min.  The default 0.01 is the lower end of the fitted domain (Sec. 4.2).  The paper's
+ * "fast" rate returns zero below chi = 0.3, where W_pair <~ 9.1e-6 alpha rho / gamma
+ * (Sec. 4.2, App. A functions 7 and 12): set 0.3 for it.  chi_min must lie in
+ * [0.01, 2000], else SFQ_ERR_ARG. */
+sfq_status sfq_set_pair_rate_cutoff(sfq_ctx *ctx, double chi_min);
+
+/* Coefficient count of the energy samplers, the accuracy/speed knob of Sec. 4.5.  Each
+ * piece of the two inverse-CDF tables holds n x n coefficients: n = 9 in binary32 and
+ * n = 12 in binary64.  With k < n, every piece is rewritten once in the Chebyshev basis,
+ * cut to its leading k x k coefficients, returned to monomials and uploaded.  The samplers
+ * of sfq_sample_*_xi and of the Monte Carlo steps then evaluate k x k coefficients per
+ * event.  Fewer loads and FMAs, a larger error.  Worst cases relative to the full table
+ * (evaluated on a grid of every piece): binary32 w-bar (photon) 6.3e-7 at k = 8 and 3.6e-6
+ * at k = 7, 1 - v-bar (pair) 1.7e-6 and 8.6e-6; binary64 w-bar 6.5e-12 at k = 11 and
+ * 6.2e-11 at k = 10, 1 - v-bar 2.2e-11 and 2.0e-10.  The photon fraction xi inherits up to
+ * three times the error of w-bar.  k must be n, n - 1 or n - 2,
+ * else SFQ_ERR_ARG; k = n restores the full tables.  The call allocates device memory and
+ * synchronises the device: make it outside stream capture, between runs.  The learned
+ * surrogate's fallback keeps the full tables.  sfq_sampler_coefficients returns n and the
+ * current k. */
+sfq_status sfq_set_sampler_coefficients(sfq_ctx *ctx, int32_t k);
+sfq_status sfq_sampler_coefficients(const sfq_ctx *ctx, int32_t *n, int32_t *k);
+
 /* Autotuner: times every launch shape of sfq_mc_step (kernel variant, particles per lane
  * or warps per block) on a copy of up to `sample_n` particles of `p` (the caller's state
  * is not modified; the copy lives in temporary device memory for the duration of the
@@ -329,6 +357,25 @@ sfq_status sfq_mlp_calibrate(sfq_mlp *m, float tol_u, int32_t *n_flagged, float 
  * plain sampler (counted in counters->surrogate_fallbacks). */
 sfq_status sfq_mlp_sample_photon_xi(sfq_mlp *m, int64_t n, const void *chi, const void *r, void *xi, void *xi_c,
                                     int32_t use_flags, sfq_counters *counters, void *stream);
+
+/* The same network for pair creation (f4): a second surrogate object stands for the
+ * inverse CDF of Eq. again_pp.  Input u = |r'| = |2r - 1| and chi in [0.1, 100]:
+ * x1 = (ln chi - C) / S with C, S centring ln chi in [ln 0.1, ln 100] on [-1, 1],
+ * x2 = -ln(1 - u) / 8 - 1; the sampler variable is ln(-ln y) with y = 1 - v-bar, the
+ * network output that variable minus ln u (-ln y ~ v-bar ~ u as u -> 0), so that
+ * y = exp(-u e^output) <= 1; the electron share is xi_e = (1 + sgn(r') v-bar) / 2, the
+ * positron's 1 - xi_e (Eq. return_to_nrg).  sfq_mlp_train, _loss_grad, _predict_lnw
+ * (which returns ln(-ln y)), _plain_targets (ln(-ln y) of the fitted pair sampler, NaN
+ * where 1 - y falls below the binary32 table's resolution, |r'| below about 1e-5) and
+ * _calibrate work on either kind; training and the loss skip samples whose target is not
+ * finite.
+ * sfq_mlp_sample_pair_xi writes real[n] xi_e and, if xi_p != NULL, xi_p with relative
+ * precision; draws outside the chi range or in flagged cells use the fitted pair
+ * sampler.  Calling the sampler of the other kind returns SFQ_ERR_ARG.  The paper has no
+ * surrogate. */
+sfq_status sfq_mlp_create_pair(sfq_ctx *ctx, uint64_t seed, sfq_mlp **out);
+sfq_status sfq_mlp_sample_pair_xi(sfq_mlp *m, int64_t n, const void *chi, const void *r, void *xi_e, void *xi_p,
+                                  int32_t use_flags, struct sfq_counters *counters, void *stream);
 
 /* Launch shape of sfq_mc_step for this context, the knob the autotuner turns.
  *   variant: 0 = automatic; 1 = warp-streaming kernel (each warp loads its particles

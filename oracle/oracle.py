@@ -262,6 +262,24 @@ def itilde_pe_upper_batch(w, chi):
     return out
 
 
+def itilde_pp_batch(v, chi):
+    """I~_pp(v, chi) (Eq. tilde_I_pp) for arrays."""
+    v, c = np.broadcast_arrays(_f64(v), _f64(chi))
+    v, c = _f64(v), _f64(c)
+    out = np.empty_like(v)
+    lib().orc_batch_itilde_pp(_I64(v.size), _p(v), _p(c), _p(out))
+    return out
+
+
+def itilde_pp_upper_y_batch(y, chi):
+    """The integral of Eq. tilde_I_pp from 1 - y to 1, integrated in y, for arrays."""
+    y, c = np.broadcast_arrays(_f64(y), _f64(chi))
+    y, c = _f64(y), _f64(c)
+    out = np.empty_like(y)
+    lib().orc_batch_itilde_pp_upper_y(_I64(y.size), _p(y), _p(c), _p(out))
+    return out
+
+
 def philox(ids, step, tag, seed):
     ids = np.ascontiguousarray(np.asarray(ids, dtype=np.uint64))
     out = np.empty((ids.size, 4), dtype=np.uint32)

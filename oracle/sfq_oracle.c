@@ -574,6 +574,10 @@ void orc_batch_itilde_pp(int64_t n, const double *v, const double *chi, double *
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t i = 0; i < n; ++i) out[i] = orc_itilde_pp(v[i], chi[i]);
 }
+void orc_batch_itilde_pp_upper_y(int64_t n, const double *y, const double *chi, double *out) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < n; ++i) out[i] = orc_itilde_pp_upper_y(y[i], chi[i]);
+}
 void orc_batch_philox(int64_t n, const uint64_t *id, uint32_t step, uint32_t tag, uint64_t seed,
                       uint32_t *out4) {
     const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};

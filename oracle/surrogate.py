@@ -2,7 +2,8 @@
 
 Two plain FP64 references, used only by the test-suite:
 
-1. ``DenseCDF`` -- the photon-emission energy CDF of the oracle,
+1. ``DenseCDF`` -- the photon-emission energy CDF of the oracle (``DensePairCDF``
+   the same for the pair shares),
    F(xi | chi) = I~_pe(w, chi) / W~_rad(chi) with s = xi / (1 - xi) = 3 chi w^3 / 2
    (Eq. pe_eff_int_2, Eq. wtilde, Eq. subs_altri), tabulated by the oracle's own
    quadrature on a dense grid of (ln chi, ln w) and interpolated by a bicubic
@@ -122,6 +123,94 @@ class DenseCDF:
         return s / (1.0 + s)
 
 
+# --- dense CDF of the pair shares --------------------------------------------------------
+PLNCHI_LO, PLNCHI_HI, PDX = np.log(0.05), np.log(200.0), 0.1
+PS_LO, PS_HI, PDS = -8.0, 19.5, 0.05
+
+
+def _expit(x):
+    return 0.5 * (1.0 + np.tanh(0.5 * np.asarray(x, np.float64)))
+
+
+class DensePairCDF:
+    """The pair-creation CDF of the oracle in the half-domain of Eq. again_pp:
+    a(y | chi) = I~_pp(1 - y, chi) / W~_pair(chi) with y = 1 - v-bar (Eq. tilde_I_pp), the
+    probability that |r'| falls below the value that returns v-bar.  logit a = ln I~_pp(v)
+    - ln int_{1-y}^1 (the two parts integrated separately, each in its own variable, so that
+    both tails keep their relative precision) is tabulated on a (ln chi, s) grid with
+    s = logit y = ln(y / v) and interpolated by a bicubic spline (a library primitive).
+    Above the grid (v -> 0) a ~ v, so logit a continues with slope -1 in s.  Where the upper
+    part underflows (small chi, small y) logit a is capped at 60."""
+
+    def __init__(self, ds=PDS, dx=PDX, cache=True):
+        from scipy.interpolate import RectBivariateSpline
+        self.x = np.arange(PLNCHI_LO, PLNCHI_HI + 0.5 * dx, dx)
+        self.s = np.arange(PS_LO, PS_HI + 0.5 * ds, ds)
+        key = hashlib.sha1(np.concatenate([self.x, self.s, [60.0]]).tobytes()).hexdigest()[:16]
+        path = os.path.join(_CACHE, f"nbw_cdf_{key}.npz")
+        z = None
+        if cache and os.path.exists(path):
+            z = np.load(path)["logit"]
+        if z is None:
+            X, S = np.meshgrid(self.x, self.s, indexing="ij")
+            chi = np.exp(X).ravel()
+            y = _expit(S).ravel()
+            v = _expit(-S).ravel()
+            lo = O.itilde_pp_batch(v, chi)
+            up = O.itilde_pp_upper_y_batch(y, chi)
+            # far in the upper tail (small chi and y) the upper part underflows; logit a is
+            # capped at 60 there, far beyond binary32 draws (logit a <= ln 2^24 = 16.6)
+            ok = (lo > 0.0) & (up > 0.0)
+            z = np.full(lo.shape, 60.0)
+            z[ok] = np.minimum(np.log(lo[ok]) - np.log(up[ok]), 60.0)
+            z[(lo <= 0.0) & (up > 0.0)] = -60.0
+            z = z.reshape(X.shape)
+            if cache:
+                os.makedirs(_CACHE, exist_ok=True)
+                tmp = path + f".tmp{os.getpid()}.npz"
+                np.savez(tmp, logit=z)
+                os.replace(tmp, path)
+        self.logit_grid = z
+        self.spline = RectBivariateSpline(self.x, self.s, z, kx=3, ky=3, s=0)
+
+    def logit(self, lnchi, s):
+        lnchi = np.clip(np.asarray(lnchi, np.float64), self.x[0], self.x[-1])
+        s = np.asarray(s, np.float64)
+        sc = np.clip(s, self.s[0], self.s[-1])
+        z = self.spline.ev(lnchi, sc)
+        hi = s > self.s[-1]
+        if np.any(hi):
+            z[hi] = z[hi] - (s[hi] - self.s[-1])
+        return z
+
+    def cdf_y(self, chi, y):
+        y = np.asarray(y, np.float64)
+        return _expit(self.logit(np.log(chi), np.log(y) - np.log1p(-y)))
+
+    def pit(self, chi, xe, xp):
+        """a = F(v-bar | chi) of sampled shares: y = 2 min(xe, xp), v-bar = |xe - xp|."""
+        xe = np.asarray(xe, np.float64)
+        xp = np.asarray(xp, np.float64)
+        y = 2.0 * np.minimum(xe, xp)
+        v = np.abs(xe - xp)
+        return _expit(self.logit(np.log(np.asarray(chi, np.float64)), np.log(y) - np.log(v)))
+
+    def inverse_lny(self, chi, a, iters=56):
+        """ln y with a(y | chi) = a, by bisection in s on the monotone spline."""
+        lnchi = np.log(np.asarray(chi, np.float64))
+        a = np.asarray(a, np.float64)
+        target = np.log(a) - np.log1p(-a)
+        lo = np.full(a.shape, self.s[0])
+        hi = np.full(a.shape, self.s[-1] + 40.0)
+        for _ in range(iters):
+            m = 0.5 * (lo + hi)
+            above = self.logit(lnchi, m) > target          # logit a falls as s rises
+            lo = np.where(above, m, lo)
+            hi = np.where(above, hi, m)
+        s = 0.5 * (lo + hi)
+        return -np.logaddexp(0.0, -s)                     # ln y = ln expit(s)
+
+
 # --- the surrogate network ------------------------------------------------------------
 # It approximates the inverse CDF of Eq. again in the paper's own variable w-bar:
 #   features  x1 = (ln chi - C_CHI) / S_CHI,  x2 = L / 8 - 1  with  L = -ln(1 - u),
@@ -169,17 +258,24 @@ def dsilu(z):
     return s * (1.0 + z * (1.0 - s))
 
 
-def features(lnchi, u):
+# the pair-creation kind: chi in [0.1, 100], input u = |r'|, sampler variable ln(-ln y)
+# with y = 1 - v-bar; the network output is that variable minus ln u
+P_C_CHI = 0.5 * (np.log(0.1) + np.log(100.0))
+P_S_CHI = 0.5 * (np.log(100.0) - np.log(0.1))
+
+
+def features(lnchi, u, kind="photon"):
     u = np.asarray(u, np.float64)
-    return np.stack([(np.asarray(lnchi, np.float64) - C_CHI) / S_CHI, -np.log1p(-u) * L_SCALE - 1.0], 1)
+    c, sc = (P_C_CHI, P_S_CHI) if kind == "pair" else (C_CHI, S_CHI)
+    return np.stack([(np.asarray(lnchi, np.float64) - c) / sc, -np.log1p(-u) * L_SCALE - 1.0], 1)
 
 
-def mlp_forward(theta, lnchi, u, quantize=False, keep=False):
+def mlp_forward(theta, lnchi, u, quantize=False, keep=False, kind="photon"):
     """The network output y for each (ln chi, u).  With quantize, the weights of every
     layer and the inputs of layers 2-4 are rounded to bfloat16 (layer 1 takes the
     binary32 features), as the inference kernel does; biases stay binary32."""
     layers = unpack(theta)
-    a = features(lnchi, u)
+    a = features(lnchi, u, kind)
     cache = []
     for l, (W, b) in enumerate(layers):
         Wq = bf16(W) if quantize else W
@@ -221,3 +317,14 @@ def mlp_loss_grad(theta, lnchi, u, target_lnw, quantize=False):
     grads.reverse()
     flat = np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads])
     return loss, flat
+
+
+def surrogate_pair_shares(theta, chi, r, quantize=False):
+    """Electron and positron shares of the pair-kind network: ln(-ln y) = network + ln |r'|,
+    y = 1 - v-bar (-ln y ~ v-bar ~ |r'| as |r'| -> 0, and y <= 1 for any output)."""
+    r = np.asarray(r, np.float64)
+    rp = 2.0 * r - 1.0
+    a = np.abs(rp)
+    y = np.exp(-a * np.exp(mlp_forward(theta, np.log(np.asarray(chi, np.float64)), a, quantize, kind="pair")))
+    small, big = 0.5 * y, 1.0 - 0.5 * y
+    return np.where(rp >= 0.0, big, small), np.where(rp >= 0.0, small, big)

@@ -186,7 +186,8 @@ void sfq_finalize(sfq_ctx *ctx) {
     {
         DeviceGuard g(ctx->device);
         sfq::release_graphs(ctx);
-        void *ptrs[6] = {ctx->d_nlc_rate, ctx->d_nbw_rate, ctx->d_nlc_inv, ctx->d_nbw_inv, ctx->d_k23, ctx->d_ki13};
+        void *ptrs[8] = {ctx->d_nlc_rate, ctx->d_nbw_rate, ctx->d_nlc_inv, ctx->d_nbw_inv, ctx->d_k23, ctx->d_ki13,
+                         ctx->d_nlc_inv_r, ctx->d_nbw_inv_r};
         for (void *p : ptrs)
             if (p) cudaFree(p);
     }
@@ -212,7 +213,7 @@ static sfq_status rate_common(sfq_ctx *ctx, int64_t n, const void *gamma, const 
         return fail(ctx, SFQ_ERR_ARG, "misaligned buffer (16 bytes required)");
     DeviceGuard g(ctx->device);
     sfq::RateLaunch L{n, gamma, chi, rate, pair ? ctx->d_nbw_rate : ctx->d_nlc_rate, ctx->pref, counters,
-                      (cudaStream_t)stream, grid_for(ctx, n, 256 * 4)};
+                      (cudaStream_t)stream, grid_for(ctx, n, 256 * 4), ctx->pair_chi_min};
     const cudaError_t e = is_fp64(ctx) ? sfq::launch_rate_f64(L, pair) : sfq::launch_rate_f32(L, pair);
     return e == cudaSuccess ? SFQ_OK : cuda_fail(ctx, e, pair ? "sfq_pair_rate" : "sfq_photon_rate");
 }
@@ -252,8 +253,7 @@ static sfq_status sample_common(sfq_ctx *ctx, int64_t n, const void *chi, const 
         (counters && !aligned8(counters)))
         return fail(ctx, SFQ_ERR_ARG, "misaligned buffer (16 bytes required)");
     DeviceGuard g(ctx->device);
-    sfq::SampleLaunch L{n, chi, r, a, b, pair ? ctx->d_nbw_inv : ctx->d_nlc_inv, counters, (cudaStream_t)stream,
-                        grid_for(ctx, n, 256 * 4)};
+    sfq::SampleLaunch L{n, chi, r, a, b, ctx, counters, (cudaStream_t)stream, grid_for(ctx, n, 256 * 4)};
     const cudaError_t e = is_fp64(ctx) ? sfq::launch_sample_f64(L, pair) : sfq::launch_sample_f32(L, pair);
     return e == cudaSuccess ? SFQ_OK : cuda_fail(ctx, e, pair ? "sfq_sample_pair_xi" : "sfq_sample_photon_xi");
 }
@@ -295,6 +295,52 @@ sfq_status sfq_mc_run_fused(sfq_ctx *ctx, const sfq_particles *p, const sfq_fiel
     const cudaError_t e = ctx->cfg.precision == SFQ_FP64 ? sfq::launch_fused_f64(L, nsteps)
                                                          : sfq::launch_fused_f32(L, nsteps);
     return e == cudaSuccess ? SFQ_OK : cuda_fail(ctx, e, "sfq_mc_run_fused");
+}
+
+sfq_status sfq_set_pair_rate_cutoff(sfq_ctx *ctx, double chi_min) {
+    if (!ctx) return SFQ_ERR_ARG;
+    if (!(chi_min >= 0.01) || !(chi_min <= 2000.0))
+        return fail(ctx, SFQ_ERR_ARG, "pair-rate cutoff outside [0.01, 2000]");
+    ctx->pair_chi_min = chi_min;
+    return SFQ_OK;
+}
+
+sfq_status sfq_set_sampler_coefficients(sfq_ctx *ctx, int32_t k) {
+    if (!ctx) return SFQ_ERR_ARG;
+    const int n = sfq::inv_coefficients(ctx->cfg.precision);
+    if (k < n - 2 || k > n) return fail(ctx, SFQ_ERR_ARG, "coefficients per variable must be n, n - 1 or n - 2");
+    const int tr = n - k;
+    DeviceGuard g(ctx->device);
+    void *nlc = nullptr, *nbw = nullptr;
+    if (tr > 0) {
+        const std::vector<unsigned char> hn = sfq::truncated_inv_table(ctx->cfg.precision, false, tr);
+        const std::vector<unsigned char> hb = sfq::truncated_inv_table(ctx->cfg.precision, true, tr);
+        cudaError_t e = cudaMalloc(&nlc, hn.size());
+        if (e == cudaSuccess) e = cudaMalloc(&nbw, hb.size());
+        if (e == cudaSuccess) e = cudaMemcpy(nlc, hn.data(), hn.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(nbw, hb.data(), hb.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            if (nlc) cudaFree(nlc);
+            if (nbw) cudaFree(nbw);
+            return cuda_fail(ctx, e, "sfq_set_sampler_coefficients");
+        }
+    }
+    // work queued with the previous tables finishes before they are freed
+    cudaDeviceSynchronize();
+    if (ctx->d_nlc_inv_r) cudaFree(ctx->d_nlc_inv_r);
+    if (ctx->d_nbw_inv_r) cudaFree(ctx->d_nbw_inv_r);
+    ctx->d_nlc_inv_r = nlc;
+    ctx->d_nbw_inv_r = nbw;
+    ctx->inv_tr = tr;
+    return SFQ_OK;
+}
+
+sfq_status sfq_sampler_coefficients(const sfq_ctx *ctx, int32_t *n, int32_t *k) {
+    if (!ctx) return SFQ_ERR_ARG;
+    const int nn = sfq::inv_coefficients(ctx->cfg.precision);
+    if (n) *n = nn;
+    if (k) *k = nn - ctx->inv_tr;
+    return SFQ_OK;
 }
 
 sfq_status sfq_set_step_shape(sfq_ctx *ctx, int32_t variant, int32_t ppt, int32_t grid_blocks) {

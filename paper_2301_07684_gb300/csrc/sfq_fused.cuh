@@ -43,8 +43,8 @@ struct FusedCfg {
 };
 
 // kstep: k_step mod K; off0: (step0 k_step) mod K.
-template <typename T, int PPL>
-__global__ void __launch_bounds__(FUSED_BS) mc_fused_kernel(const StepArgs<T> a, uint32_t step0, uint32_t nsteps,
+template <typename T, int PPL, bool TRUNC = false>
+__global__ void __launch_bounds__(FUSED_BS, 2) mc_fused_kernel(const StepArgs<T> a, uint32_t step0, uint32_t nsteps,
                                                             uint32_t off0, uint32_t kstep) {
     using Q = L<T>;
     using CFG = FusedCfg<T, PPL>;
@@ -148,7 +148,8 @@ __global__ void __launch_bounds__(FUSED_BS) mc_fused_kernel(const StepArgs<T> a,
                 FEntry<T> e{};
                 if (v) e = q[(qh + lane) & (QS - 1)];
                 EvOut<T> o;
-                process_events_core<T>(a, e.step, e.i, e.g, e.chi, (T)-1, e.px, e.py, e.pz, (uint8_t)e.fl, v, c, o);
+                process_events_core<T, TRUNC>(a, e.step, e.i, e.g, e.chi, (T)-1, e.px, e.py, e.pz, (uint8_t)e.fl, v,
+                                              c, o);
                 if (v) res[(qh + lane) & (QS - 1)] = o;
                 __syncwarp();
                 // the waiting slots take their new state and finish their step

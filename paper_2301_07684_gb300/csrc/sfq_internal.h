@@ -20,6 +20,9 @@ struct sfq_ctx {
     std::vector<std::pair<std::string, cudaGraphExec_t>> graphs;   // sfq_mc_run cache
     int step_ppt = 0;        // 0 = default
     int step_grid = 0;       // 0 = one wave of resident blocks
+    double pair_chi_min = 0.01;   // NBW rate is zero below this chi (sfq_set_pair_rate_cutoff)
+    int inv_tr = 0;               // inverse-CDF coefficients dropped per variable (sfq_set_sampler_coefficients)
+    void *d_nlc_inv_r = nullptr, *d_nbw_inv_r = nullptr;   // the truncated tables when inv_tr > 0
     std::string err;
 };
 
@@ -35,12 +38,13 @@ struct RateLaunch {
     sfq_counters *counters;
     cudaStream_t stream;
     int grid;
+    double pair_chi_min;
 };
 struct SampleLaunch {
     int64_t n;
     const void *chi, *r;
     void *a, *b;
-    const void *inv;
+    const sfq_ctx *ctx;      // tables (full or truncated) of the context
     sfq_counters *counters;
     cudaStream_t stream;
     int grid;
@@ -70,6 +74,13 @@ cudaError_t launch_uniforms_f64(int64_t n, const uint64_t *id, uint32_t step, ui
 cudaError_t launch_step_f32(const StepLaunch &);
 cudaError_t launch_step_f64(const StepLaunch &);
 cudaError_t launch_fused_f32(const StepLaunch &, uint32_t nsteps);
+// the same with the truncated samplers compiled in (sfq_launch_tr_f32.cu / _f64.cu)
+cudaError_t launch_step_trunc_f32(const StepLaunch &);
+cudaError_t launch_step_trunc_f64(const StepLaunch &);
+cudaError_t launch_fused_trunc_f32(const StepLaunch &, uint32_t nsteps);
+cudaError_t launch_fused_trunc_f64(const StepLaunch &, uint32_t nsteps);
+cudaError_t prepare_step_trunc_f32();
+cudaError_t prepare_step_trunc_f64();
 cudaError_t launch_fused_f64(const StepLaunch &, uint32_t nsteps);
 
 sfq_status validate_step(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, const sfq_products *out,
@@ -90,5 +101,9 @@ struct HostTables {
     size_t nlc_rate_bytes, nbw_rate_bytes, nlc_inv_bytes, nbw_inv_bytes, k23_bytes, ki13_bytes;
 };
 HostTables host_tables(int precision);
+// Inverse-CDF table with every piece's (n x n) coefficients truncated to (n - tr) x (n - tr)
+// in the Chebyshev basis, rows padded to 16 bytes (sfq_tables_host.cu).
+std::vector<unsigned char> truncated_inv_table(int precision, bool pair, int tr);
+int inv_coefficients(int precision);   // n of the context's inverse-CDF tables
 
 }  // namespace sfq

@@ -52,6 +52,10 @@ SFQ_LAYOUT(double, F64)
 template <typename T>
 struct Tables {
     const T *nlc_rate, *nbw_rate, *nlc_inv, *nbw_inv, *k23, *ki13;
+    // inverse-CDF tables truncated to (n - tr) x (n - tr) coefficients per piece (tr = 1 or 2),
+    // used by the samplers when tr > 0 (the coefficient-count knob of Sec. 4.5)
+    const T *nlc_inv_r, *nbw_inv_r;
+    int tr;
 };
 
 // Rate tables in shared memory: each piece padded to a multiple of 16 bytes so that
@@ -128,11 +132,13 @@ __device__ __forceinline__ float exp_m83(float chi) {
 }
 __device__ __forceinline__ double exp_m83(double chi) { return exp(-(8.0 / 3.0) / chi); }
 
-// W~_pair(chi) = chi h(chi) exp(-8/(3 chi)) (Eq. wtilde_pair); zero below 0.01 (Sec. 4.2).
+// W~_pair(chi) = chi h(chi) exp(-8/(3 chi)) (Eq. wtilde_pair); zero below chi_min, which is
+// 0.01, the lower end of the fitted domain (Sec. 4.2), or larger for the "fast" rate that
+// neglects pair creation below e.g. chi = 0.3 (Sec. 4.2).
 template <typename T>
-__device__ __forceinline__ T wtilde_pair(const T *c, T chi, bool &oor) {
+__device__ __forceinline__ T wtilde_pair(const T *c, T chi, bool &oor, T chi_min = (T)0.01) {
     using Q = L<T>;
-    if (!(chi >= (T)0.01)) return (T)0;
+    if (!(chi >= chi_min)) return (T)0;
     T x;
     constexpr int ST = RateSmem<T>::NBW_STRIDE;
     const int p = octave_piece<T, Q::NBW_ELO, Q::NBW_EHI, Q::NBW_SUB, Q::NBW_LOW, Q::NBW_SUBLOW>(chi, x, oor);
@@ -140,16 +146,18 @@ __device__ __forceinline__ T wtilde_pair(const T *c, T chi, bool &oor) {
     return chi * h * exp_m83(chi);
 }
 
-// s = 3 chi w^3 / 2 for w-bar = G~_pe(r, chi) (Eq. again, Eq. subs_altri).
-template <typename T>
+// s = 3 chi w^3 / 2 for w-bar = G~_pe(r, chi) (Eq. again, Eq. subs_altri).  TR > 0 reads the
+// table truncated by TR degrees in each variable.
+template <typename T, int TR = 0>
 __device__ __forceinline__ T photon_s(const T *__restrict__ inv, T chi, T r, bool &oor) {
     using Q = L<T>;
+    constexpr int DX = Q::PI_DX - TR, DY = Q::PI_DY - TR;
     T xc, xr;
     bool low;
     const int ic = octave_piece<T, Q::PI_XELO, Q::PI_XEHI, Q::PI_XSUB, Q::PI_XLOW, Q::PI_XSUBLOW>(chi, xc, oor);
     const int ir = prob_piece<T, Q::PI_YE0, Q::PI_YSUB, Q::PI_YSUBLOW, Q::PI_YQLO, Q::PI_YSUBQ>(r, xr, low, oor);
-    const T *c = inv + ((size_t)ic * Q::PI_NY + ir) * ((Q::PI_DX + 1) * padded_row(Q::PI_DY + 1, sizeof(T)));
-    T w = horner2<Q::PI_DX, Q::PI_DY>(c, xc, xr);
+    const T *c = inv + ((size_t)ic * Q::PI_NY + ir) * ((DX + 1) * padded_row(DY + 1, sizeof(T)));
+    T w = horner2<DX, DY>(c, xc, xr);
     if (low) w *= r;                          // the low-r block holds w-bar / r
     const T chi_eff = chi > (T)4096 ? (T)4096 : chi;
     return (T)1.5 * chi_eff * w * w * w;
@@ -157,20 +165,48 @@ __device__ __forceinline__ T photon_s(const T *__restrict__ inv, T chi, T r, boo
 
 // Electron and positron shares for r (Eq. again_pp, Eq. return_to_nrg): the table
 // holds y = 1 - v-bar as a function of (chi, |r'|).
-template <typename T>
-__device__ __forceinline__ void pair_shares(const T *__restrict__ inv, T chi, T r, T &xe, T &xp, bool &oor) {
+// y = 1 - v-bar at a = |r'| (Eq. again_pp): the table's value.
+template <typename T, int TR = 0>
+__device__ __forceinline__ T pair_y(const T *__restrict__ inv, T chi, T a, bool &oor) {
     using Q = L<T>;
-    const T rp = (T)2 * r - (T)1;
-    const T a = fabs(rp);
+    constexpr int DX = Q::PP_DX - TR, DY = Q::PP_DY - TR;
     T xc, xr;
     bool low;
     const int ic = octave_piece<T, Q::PP_XELO, Q::PP_XEHI, Q::PP_XSUB, Q::PP_XLOW, Q::PP_XSUBLOW>(chi, xc, oor);
     const int ir = prob_piece<T, Q::PP_YE0, Q::PP_YSUB, Q::PP_YSUBLOW, Q::PP_YQLO, Q::PP_YSUBQ>(a, xr, low, oor);
-    const T *c = inv + ((size_t)ic * Q::PP_NY + ir) * ((Q::PP_DX + 1) * padded_row(Q::PP_DY + 1, sizeof(T)));
-    const T y = horner2<Q::PP_DX, Q::PP_DY>(c, xc, xr);
+    const T *c = inv + ((size_t)ic * Q::PP_NY + ir) * ((DX + 1) * padded_row(DY + 1, sizeof(T)));
+    return horner2<DX, DY>(c, xc, xr);
+}
+
+template <typename T, int TR = 0>
+__device__ __forceinline__ void pair_shares(const T *__restrict__ inv, T chi, T r, T &xe, T &xp, bool &oor) {
+    const T rp = (T)2 * r - (T)1;
+    const T y = pair_y<T, TR>(inv, chi, fabs(rp), oor);
     const T small = (T)0.5 * y, big = (T)1 - small;
     if (rp >= (T)0) { xe = big; xp = small; }
     else { xe = small; xp = big; }
+}
+
+// The samplers with the coefficient count compiled into the kernel.  TRUNC = false reads the
+// full tables.  TRUNC = true reads the tables truncated by t.tr = 1 or 2 degrees in each
+// variable.  Kernels are instantiated with TRUNC = true only for contexts that use the
+// knob, so the default kernels carry no code for it.
+template <typename T, bool TRUNC>
+__device__ __forceinline__ T photon_s_sel(const Tables<T> &t, T chi, T r, bool &oor) {
+    if (TRUNC) {
+        if (t.tr == 2) return photon_s<T, 2>(t.nlc_inv_r, chi, r, oor);
+        return photon_s<T, 1>(t.nlc_inv_r, chi, r, oor);
+    }
+    return photon_s<T, 0>(t.nlc_inv, chi, r, oor);
+}
+template <typename T, bool TRUNC>
+__device__ __forceinline__ void pair_shares_sel(const Tables<T> &t, T chi, T r, T &xe, T &xp, bool &oor) {
+    if (TRUNC) {
+        if (t.tr == 2) pair_shares<T, 2>(t.nbw_inv_r, chi, r, xe, xp, oor);
+        else pair_shares<T, 1>(t.nbw_inv_r, chi, r, xe, xp, oor);
+        return;
+    }
+    pair_shares<T, 0>(t.nbw_inv, chi, r, xe, xp, oor);
 }
 
 // ln of the photon spectrum Eq. pe_dp at u = eps_gamma/(eps_e - eps_gamma), without the
@@ -234,7 +270,7 @@ template <typename T, bool PAIR>
 __global__ void __launch_bounds__(256) rate_kernel(int64_t n, const T *__restrict__ gamma,
                                                    const T *__restrict__ chi, T *__restrict__ rate,
                                                    const T *__restrict__ table, T pref,
-                                                   sfq_counters *counters) {
+                                                   sfq_counters *counters, T pair_chi_min) {
     using RS = RateSmem<T>;
     constexpr int N = PAIR ? RS::NBW_N : RS::NLC_N;
     __shared__ __align__(16) T tab[N];
@@ -255,7 +291,7 @@ __global__ void __launch_bounds__(256) rate_kernel(int64_t n, const T *__restric
             ++c.v[C_NAN];
             r = (T)0;
         } else if (PAIR) {
-            r = pref * wtilde_pair<T>(tab, x, oor) / g;
+            r = pref * wtilde_pair<T>(tab, x, oor, pair_chi_min) / g;
         } else {
             r = pref * (x / g) * wtilde_rad<T>(tab, x, oor);
         }
@@ -266,10 +302,10 @@ __global__ void __launch_bounds__(256) rate_kernel(int64_t n, const T *__restric
 }
 
 // Batched samplers (App. A functions 9 and 11, Eqs. again, again_pp).
-template <typename T, bool PAIR>
+template <typename T, bool PAIR, bool TRUNC>
 __global__ void __launch_bounds__(256) sample_kernel(int64_t n, const T *__restrict__ chi,
                                                      const T *__restrict__ r, T *__restrict__ out_a,
-                                                     T *__restrict__ out_b, const T *__restrict__ inv,
+                                                     T *__restrict__ out_b, const Tables<T> tab,
                                                      sfq_counters *counters) {
     Cnt c;
     c.zero();
@@ -284,11 +320,11 @@ __global__ void __launch_bounds__(256) sample_kernel(int64_t n, const T *__restr
         }
         if (PAIR) {
             T xe, xp;
-            pair_shares<T>(inv, x, u, xe, xp, oor);
+            pair_shares_sel<T, TRUNC>(tab, x, u, xe, xp, oor);
             out_a[i] = xe;
             if (out_b) out_b[i] = xp;
         } else {
-            const T s = photon_s<T>(inv, x, u, oor);
+            const T s = photon_s_sel<T, TRUNC>(tab, x, u, oor);
             const T inv1s = (T)1 / ((T)1 + s);
             out_a[i] = s * inv1s;          // xi = s/(1+s)
             if (out_b) out_b[i] = inv1s;   // 1 - xi

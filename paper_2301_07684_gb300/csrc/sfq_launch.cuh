@@ -16,6 +16,9 @@ static Tables<T> tables_of(const sfq_ctx *ctx) {
     t.nbw_inv = static_cast<const T *>(ctx->d_nbw_inv);
     t.k23 = static_cast<const T *>(ctx->d_k23);
     t.ki13 = static_cast<const T *>(ctx->d_ki13);
+    t.nlc_inv_r = static_cast<const T *>(ctx->d_nlc_inv_r);
+    t.nbw_inv_r = static_cast<const T *>(ctx->d_nbw_inv_r);
+    t.tr = ctx->inv_tr;
     return t;
 }
 
@@ -26,9 +29,11 @@ static cudaError_t launch_rate_t(const RateLaunch &L, bool pair) {
     T *out = static_cast<T *>(L.rate);
     const T *tab = static_cast<const T *>(L.table);
     if (pair)
-        rate_kernel<T, true><<<L.grid, 256, 0, L.stream>>>(L.n, g, x, out, tab, (T)L.pref, L.counters);
+        rate_kernel<T, true><<<L.grid, 256, 0, L.stream>>>(L.n, g, x, out, tab, (T)L.pref, L.counters,
+                                                             (T)L.pair_chi_min);
     else
-        rate_kernel<T, false><<<L.grid, 256, 0, L.stream>>>(L.n, g, x, out, tab, (T)L.pref, L.counters);
+        rate_kernel<T, false><<<L.grid, 256, 0, L.stream>>>(L.n, g, x, out, tab, (T)L.pref, L.counters,
+                                                              (T)L.pair_chi_min);
     return cudaGetLastError();
 }
 
@@ -37,11 +42,16 @@ static cudaError_t launch_sample_t(const SampleLaunch &L, bool pair) {
     if (L.n == 0) return cudaSuccess;
     const T *x = static_cast<const T *>(L.chi), *r = static_cast<const T *>(L.r);
     T *a = static_cast<T *>(L.a), *b = static_cast<T *>(L.b);
-    const T *inv = static_cast<const T *>(L.inv);
-    if (pair)
-        sample_kernel<T, true><<<L.grid, 256, 0, L.stream>>>(L.n, x, r, a, b, inv, L.counters);
+    const Tables<T> tab = tables_of<T>(L.ctx);
+    const bool tr = tab.tr > 0;
+    if (pair && tr)
+        sample_kernel<T, true, true><<<L.grid, 256, 0, L.stream>>>(L.n, x, r, a, b, tab, L.counters);
+    else if (pair)
+        sample_kernel<T, true, false><<<L.grid, 256, 0, L.stream>>>(L.n, x, r, a, b, tab, L.counters);
+    else if (tr)
+        sample_kernel<T, false, true><<<L.grid, 256, 0, L.stream>>>(L.n, x, r, a, b, tab, L.counters);
     else
-        sample_kernel<T, false><<<L.grid, 256, 0, L.stream>>>(L.n, x, r, a, b, inv, L.counters);
+        sample_kernel<T, false, false><<<L.grid, 256, 0, L.stream>>>(L.n, x, r, a, b, tab, L.counters);
     return cudaGetLastError();
 }
 
@@ -55,21 +65,29 @@ static cudaError_t launch_uniforms_t(int64_t n, const uint64_t *id, uint32_t ste
 
 // Dynamic shared-memory limits of the TMA-staged kernels, set once per process (and before
 // any stream capture, where the launch itself is recorded).
-template <typename T>
+// The TMA-staged shapes compiled with the truncated samplers (TRUNC) are limited to 16
+// consumer warps; the warp-streaming ones to 2 particles per lane.
+constexpr int TRUNC_CW = 16, TRUNC_PPT = 2;
+
+template <typename T, bool TRUNC>
 static cudaError_t prepare_step_t() {
     static bool done = false;
     if (done) return cudaSuccess;
     cudaError_t e = cudaSuccess;
 #define SFQ_PREP(CWV)                                                                                         \
     if (e == cudaSuccess)                                                                                     \
-        e = cudaFuncSetAttribute(mc_step_tma_kernel<T, FK_SOA, CWV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 (int)tma_smem_bytes<T, FK_SOA, CWV>());                                     \
+        e = cudaFuncSetAttribute(mc_step_tma_kernel<T, FK_SOA, CWV, TRUNC>,                                  \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem_bytes<T, FK_SOA, CWV>()); \
     if (e == cudaSuccess)                                                                                     \
-        e = cudaFuncSetAttribute(mc_step_tma_kernel<T, FK_PW, CWV>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                                 (int)tma_smem_bytes<T, FK_PW, CWV>());
-    SFQ_PREP(8)
-    SFQ_PREP(16)
-    SFQ_PREP(20)
+        e = cudaFuncSetAttribute(mc_step_tma_kernel<T, FK_PW, CWV, TRUNC>,                                   \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem_bytes<T, FK_PW, CWV>());
+    if constexpr (TRUNC) {
+        SFQ_PREP(TRUNC_CW)
+    } else {
+        SFQ_PREP(8)
+        SFQ_PREP(16)
+        SFQ_PREP(20)
+    }
 #undef SFQ_PREP
     if (e == cudaSuccess) done = true;
     return e;
@@ -132,12 +150,13 @@ static StepArgs<T> make_step_args(const StepLaunch &L) {
     a.rho = (T)ctx->rho;
     a.inv_dt = (T)(1.0 / ctx->cfg.dt);
     a.inv_dt2 = (T)(1.0 / (ctx->cfg.dt * ctx->cfg.dt));
+    a.pair_chi_min = (T)ctx->pair_chi_min;
     a.tab = tables_of<T>(ctx);
     a.counters = L.counters;
     return a;
 }
 
-template <typename T>
+template <typename T, bool TRUNC>
 static cudaError_t launch_step_t(const StepLaunch &L) {
     const sfq_particles &p = *L.p;
     const sfq_fields &f = *L.f;
@@ -147,7 +166,7 @@ static cudaError_t launch_step_t(const StepLaunch &L) {
     const bool pw = f.kind == SFQ_FIELDS_PLANE_WAVE;
     // TMA-staged kernel: one persistent block per SM; chosen automatically when every
     // SM gets at least one full tile.  `ppt` selects the consumer warps per block.
-    const int cw = (L.ppt == 8 || L.ppt == 16 || L.ppt == 20) ? L.ppt : 16;
+    const int cw = TRUNC ? TRUNC_CW : ((L.ppt == 8 || L.ppt == 16 || L.ppt == 20) ? L.ppt : 16);
     const int tile = cw * (sizeof(T) == 4 ? 64 : 32);
     // the beyond-LCFA model runs on the warp-streaming kernel (its state is read directly)
     const bool tma = p.lepton_model != SFQ_LEPTON_BLCFA_LOCAL &&
@@ -157,17 +176,24 @@ static cudaError_t launch_step_t(const StepLaunch &L) {
         size_t smem = 0;
 #define SFQ_TMA_CASE(CWV)                                                                             \
     case CWV:                                                                                         \
-        kern = pw ? mc_step_tma_kernel<T, FK_PW, CWV> : mc_step_tma_kernel<T, FK_SOA, CWV>;             \
+        kern = pw ? mc_step_tma_kernel<T, FK_PW, CWV, TRUNC> : mc_step_tma_kernel<T, FK_SOA, CWV, TRUNC>; \
         smem = pw ? tma_smem_bytes<T, FK_PW, CWV>() : tma_smem_bytes<T, FK_SOA, CWV>();                 \
         break;
-        switch (cw) {
-            SFQ_TMA_CASE(8)
-            SFQ_TMA_CASE(20)
-            default:
-            SFQ_TMA_CASE(16)
+        if constexpr (TRUNC) {
+            switch (cw) {
+                default:
+                SFQ_TMA_CASE(TRUNC_CW)
+            }
+        } else {
+            switch (cw) {
+                SFQ_TMA_CASE(8)
+                SFQ_TMA_CASE(20)
+                default:
+                SFQ_TMA_CASE(16)
+            }
         }
 #undef SFQ_TMA_CASE
-        cudaError_t e = prepare_step_t<T>();
+        cudaError_t e = prepare_step_t<T, TRUNC>();
         if (e != cudaSuccess) return e;
         (void)smem;
         const int64_t ntiles = (p.n + tile - 1) / tile;
@@ -177,14 +203,19 @@ static cudaError_t launch_step_t(const StepLaunch &L) {
         return cudaGetLastError();
     }
     void (*kern)(const StepArgs<T>) = nullptr;
-    switch ((pw ? 10 : 0) + L.ppt) {
-        case 1: kern = mc_step_kernel<T, FK_SOA, 1>; break;
-        case 4: kern = mc_step_kernel<T, FK_SOA, 4>; break;
-        case 11: kern = mc_step_kernel<T, FK_PW, 1>; break;
-        case 12: kern = mc_step_kernel<T, FK_PW, 2>; break;
-        case 14: kern = mc_step_kernel<T, FK_PW, 4>; break;
-        default: kern = mc_step_kernel<T, FK_SOA, 2>; break;
+    if constexpr (TRUNC) {
+        kern = pw ? mc_step_kernel<T, FK_PW, TRUNC_PPT, true> : mc_step_kernel<T, FK_SOA, TRUNC_PPT, true>;
+    } else {
+        switch ((pw ? 10 : 0) + L.ppt) {
+            case 1: kern = mc_step_kernel<T, FK_SOA, 1>; break;
+            case 4: kern = mc_step_kernel<T, FK_SOA, 4>; break;
+            case 11: kern = mc_step_kernel<T, FK_PW, 1>; break;
+            case 12: kern = mc_step_kernel<T, FK_PW, 2>; break;
+            case 14: kern = mc_step_kernel<T, FK_PW, 4>; break;
+            default: kern = mc_step_kernel<T, FK_SOA, 2>; break;
+        }
     }
+    const int ppt = TRUNC ? TRUNC_PPT : L.ppt;
     int grid = L.grid;
     if (grid <= 0) {
         // one wave of resident blocks: a multiple of the SM count
@@ -192,7 +223,7 @@ static cudaError_t launch_step_t(const StepLaunch &L) {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, STEP_BS, 0);
         if (e != cudaSuccess || per_sm < 1) per_sm = 1;
         grid = per_sm * ctx->num_sms;
-        const int64_t chunks = (p.n + 32 * L.ppt - 1) / (32 * L.ppt);
+        const int64_t chunks = (p.n + 32 * ppt - 1) / (32 * ppt);
         const int64_t need = (chunks + STEP_BS / 32 - 1) / (STEP_BS / 32);
         if (need < grid) grid = (int)(need > 0 ? need : 1);
     }
@@ -201,7 +232,7 @@ static cudaError_t launch_step_t(const StepLaunch &L) {
 }
 
 // nsteps steps from L.step on in one launch of the fused plane-wave kernel (sfq_fused.cuh).
-template <typename T>
+template <typename T, bool TRUNC>
 static cudaError_t launch_fused_t(const StepLaunch &L, uint32_t nsteps) {
     constexpr int PPL = sizeof(T) == 4 ? 4 : 2;
     using CFG = FusedCfg<T, PPL>;
@@ -209,7 +240,7 @@ static cudaError_t launch_fused_t(const StepLaunch &L, uint32_t nsteps) {
     const sfq_fields &f = *L.f;
     if (p.n == 0 || nsteps == 0) return cudaSuccess;
     const StepArgs<T> a = make_step_args<T>(L);
-    auto kern = mc_fused_kernel<T, PPL>;
+    auto kern = mc_fused_kernel<T, PPL, TRUNC>;
     static bool attr = false;
     if (!attr) {
         const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

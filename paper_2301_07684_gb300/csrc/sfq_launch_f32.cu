@@ -8,7 +8,14 @@ cudaError_t launch_uniforms_f32(int64_t n, const uint64_t *id, uint32_t step, ui
                                 cudaStream_t s, int grid) {
     return launch_uniforms_t<float>(n, id, step, tag, seed, u, s, grid);
 }
-cudaError_t launch_step_f32(const StepLaunch &L) { return launch_step_t<float>(L); }
-cudaError_t prepare_step_f32() { return prepare_step_t<float>(); }
-cudaError_t launch_fused_f32(const StepLaunch &L, uint32_t nsteps) { return launch_fused_t<float>(L, nsteps); }
+cudaError_t launch_step_f32(const StepLaunch &L) {
+    return L.ctx->inv_tr > 0 ? launch_step_trunc_f32(L) : launch_step_t<float, false>(L);
+}
+cudaError_t prepare_step_f32() {
+    const cudaError_t e = prepare_step_t<float, false>();
+    return e == cudaSuccess ? prepare_step_trunc_f32() : e;
+}
+cudaError_t launch_fused_f32(const StepLaunch &L, uint32_t nsteps) {
+    return L.ctx->inv_tr > 0 ? launch_fused_trunc_f32(L, nsteps) : launch_fused_t<float, false>(L, nsteps);
+}
 }  // namespace sfq

@@ -8,7 +8,14 @@ cudaError_t launch_uniforms_f64(int64_t n, const uint64_t *id, uint32_t step, ui
                                 cudaStream_t s, int grid) {
     return launch_uniforms_t<double>(n, id, step, tag, seed, u, s, grid);
 }
-cudaError_t launch_step_f64(const StepLaunch &L) { return launch_step_t<double>(L); }
-cudaError_t prepare_step_f64() { return prepare_step_t<double>(); }
-cudaError_t launch_fused_f64(const StepLaunch &L, uint32_t nsteps) { return launch_fused_t<double>(L, nsteps); }
+cudaError_t launch_step_f64(const StepLaunch &L) {
+    return L.ctx->inv_tr > 0 ? launch_step_trunc_f64(L) : launch_step_t<double, false>(L);
+}
+cudaError_t prepare_step_f64() {
+    const cudaError_t e = prepare_step_t<double, false>();
+    return e == cudaSuccess ? prepare_step_trunc_f64() : e;
+}
+cudaError_t launch_fused_f64(const StepLaunch &L, uint32_t nsteps) {
+    return L.ctx->inv_tr > 0 ? launch_fused_trunc_f64(L, nsteps) : launch_fused_t<double, false>(L, nsteps);
+}
 }  // namespace sfq

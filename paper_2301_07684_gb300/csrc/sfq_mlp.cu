@@ -28,6 +28,7 @@
 
 struct sfq_mlp {
     sfq_ctx *ctx;
+    int kind;                         // 0: photon emission (Eq. again), 1: pair creation (Eq. again_pp)
     float *params, *m, *v, *grad;     // binary32 master parameters, Adam moments, gradient
     uint8_t *flags;                   // fallback cells (NCELL bytes)
     float *cell_err;                  // per-cell calibration error (NCELL floats)
@@ -54,12 +55,30 @@ __device__ __forceinline__ float dsilu(float z) {
     const float s = __fdividef(1.0f, 1.0f + __expf(-z));
     return s * (1.0f + z * (1.0f - s));
 }
-__device__ __forceinline__ void features(float chi, float u, float &x1, float &x2) {
-    x1 = (logf(chi) - C_CHI) * (1.0f / S_CHI);
+// What distinguishes the two samplers the network can stand for.  Photon emission: input
+// u = r, chi in [1e-3, 100], sampler variable ln w-bar.  Pair creation: input u = |r'| =
+// |2r - 1|, chi in [0.1, 100], sampler variable ln(-ln y) with y = 1 - v-bar (Eq.
+// again_pp): -ln y ~ v-bar ~ u as u -> 0, so both variables minus ln u stay smooth at
+// u -> 0, and y = exp(-u e^network) never exceeds 1.  The network output is always the
+// sampler variable minus ln u.
+struct Kind {
+    float c_chi, inv_s_chi, chi_lo, chi_hi;
+    int pair;
+};
+constexpr float P_C_CHI = 1.1512925464970229f;      // (ln 0.1 + ln 100) / 2
+constexpr float P_S_CHI = 3.4538776394910684f;      // (ln 100 - ln 0.1) / 2
+constexpr float P_CHI_LO = 0.1f, P_CHI_HI = 100.0f;
+inline Kind kind_of(int pair) {
+    return pair ? Kind{P_C_CHI, 1.0f / P_S_CHI, P_CHI_LO, P_CHI_HI, 1} : Kind{C_CHI, 1.0f / S_CHI, CHI_LO, CHI_HI, 0};
+}
+__device__ __forceinline__ void features(const Kind &K, float chi, float u, float &x1, float &x2) {
+    x1 = (logf(chi) - K.c_chi) * K.inv_s_chi;
     x2 = -log1pf(-u) * L_SCALE - 1.0f;
 }
-__device__ __forceinline__ int cell_of(float chi, float u) {
-    const float t = (logf(chi) - logf(CHI_LO)) * (float)NCX / (logf(CHI_HI) - logf(CHI_LO));
+// network output + offset = the sampler's variable (ln w-bar or ln(-ln y))
+__device__ __forceinline__ float out_offset(const Kind &, float u) { return logf(u); }
+__device__ __forceinline__ int cell_of(const Kind &K, float chi, float u) {
+    const float t = (logf(chi) - logf(K.chi_lo)) * (float)NCX / (logf(K.chi_hi) - logf(K.chi_lo));
     int cx = (int)t, cu = (int)(u * (float)NCU);
     cx = cx < 0 ? 0 : (cx >= NCX ? NCX - 1 : cx);
     cu = cu < 0 ? 0 : (cu >= NCU ? NCU - 1 : cu);
@@ -100,6 +119,7 @@ struct TrainArgs {
     float scale;           // d loss / d y = scale * r  (2 / batch)
     float *partial;        // [gridDim.x][NP]
     float *partial_loss;   // [gridDim.x]
+    Kind K;
 };
 
 // Z[s][j] = sum_k A[s][k] W[j][k] + b[j] over the block's samples (K = 64).
@@ -201,12 +221,14 @@ __global__ void __launch_bounds__(TB) train_kernel(const TrainArgs a) {
             chi = a.chi[idx];
             u = a.u[idx];
             lw = a.lnw[idx];
+            ok = isfinite(lw);            // samples without a target (NaN) do not enter the loss
+            if (!ok) { chi = 1.0f; u = 0.5f; lw = 0.0f; }
         }
         float x1, x2;
-        features(chi, u, x1, x2);
+        features(a.K, chi, u, x1, x2);
         S.x[2 * tid] = x1;
         S.x[2 * tid + 1] = x2;
-        S.yt[tid] = lw - logf(u);
+        S.yt[tid] = lw - out_offset(a.K, u);
         S.valid[tid] = ok;
     }
     __syncthreads();
@@ -336,9 +358,9 @@ __device__ __forceinline__ void stage_simt(SimtW &W, const float *P) {
     }
     if (threadIdx.x == 0) W.b4 = P[O_B4];
 }
-__device__ __forceinline__ float forward_simt(const SimtW &W, float chi, float u) {
+__device__ __forceinline__ float forward_simt(const SimtW &W, const Kind &K, float chi, float u) {
     float x1, x2;
-    features(chi, u, x1, x2);
+    features(K, chi, u, x1, x2);
     float a[H], b[H];
 #pragma unroll
     for (int j = 0; j < H; ++j) a[j] = bf16r(silu(fmaf(W.w1[2 * j], x1, fmaf(W.w1[2 * j + 1], x2, W.b1[j]))));
@@ -362,7 +384,7 @@ __device__ __forceinline__ float forward_simt(const SimtW &W, float chi, float u
     return y;
 }
 
-__global__ void __launch_bounds__(128) predict_kernel(const float *__restrict__ P, int64_t n,
+__global__ void __launch_bounds__(128) predict_kernel(const float *__restrict__ P, const Kind K, int64_t n,
                                                       const float *__restrict__ chi, const float *__restrict__ u,
                                                       float *__restrict__ lnw) {
     __shared__ SimtW W;
@@ -370,34 +392,44 @@ __global__ void __launch_bounds__(128) predict_kernel(const float *__restrict__ 
     __syncthreads();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float uu = u[i];
-        lnw[i] = forward_simt(W, chi[i], uu) + logf(uu);
+        lnw[i] = forward_simt(W, K, chi[i], uu) + out_offset(K, uu);
     }
 }
 
 // ---------------------------------------------------------------------------------------
 // Calibration: per cell, the largest |u_net - u| implied by the network's ln w-bar against
 // the plain sampler's, |d ln w| / (d ln w / du), over 8 x 8 points of the cell.
-__device__ __forceinline__ float plain_lnw(const float *inv, float chi, float u) {
+// The plain fitted sampler's variable: ln w-bar (photon) or ln(-ln y) (pair, u = |r'|).
+__device__ __forceinline__ float plain_lnw(const Kind &K, const float *inv, float chi, float u) {
     bool oor = false;
+    if (K.pair) {
+        // -ln y from v-bar = 1 - y where y is near 1; where 1 - y falls below the binary32
+        // table's resolution (|r'| below about 1e-5) the variable is unresolved: NaN
+        const float y = pair_y<float>(inv, chi, u, oor);
+        const float v = 1.0f - y;
+        if (!(v >= 1.52587890625e-05f)) return __int_as_float(0x7fffffff);    // 2^-16
+        return logf(y < 0.5f ? -logf(y) : -log1pf(-v));
+    }
     const float s = photon_s<float>(inv, chi, u, oor);
     return (logf(2.0f * s) - logf(3.0f * chi)) * (1.0f / 3.0f);
 }
-__global__ void __launch_bounds__(64) calibrate_kernel(const float *__restrict__ P, const float *__restrict__ inv,
-                                                       float tol_u, uint8_t *__restrict__ flags,
-                                                       float *__restrict__ cell_err) {
+__global__ void __launch_bounds__(64) calibrate_kernel(const float *__restrict__ P, const Kind K,
+                                                       const float *__restrict__ inv, float tol_u,
+                                                       uint8_t *__restrict__ flags, float *__restrict__ cell_err) {
     __shared__ SimtW W;
     __shared__ float red[64];
     stage_simt(W, P);
     __syncthreads();
     const int cell = blockIdx.x, cx = cell / NCU, cu = cell % NCU;
     const int pa = threadIdx.x >> 3, pb = threadIdx.x & 7;
-    const float lo = logf(CHI_LO), span = logf(CHI_HI) - logf(CHI_LO);
+    const float lo = logf(K.chi_lo), span = logf(K.chi_hi) - logf(K.chi_lo);
     const float chi = expf(lo + span * ((float)cx + ((float)pa + 0.5f) * 0.125f) / (float)NCX);
     const float u = ((float)cu + ((float)pb + 0.5f) * 0.125f) / (float)NCU;
-    const float ln_net = forward_simt(W, chi, u) + logf(u);
-    const float ln_p = plain_lnw(inv, chi, u);
+    const float ln_net = forward_simt(W, K, chi, u) + out_offset(K, u);
+    const float ln_p = plain_lnw(K, inv, chi, u);
     const float h = 1.0f / (float)(NCU * 64);
-    const float dlnw_du = (plain_lnw(inv, chi, u + h) - plain_lnw(inv, chi, u - h)) / (2.0f * h);
+    // |d ln w / du| (both sampler variables rise with u)
+    const float dlnw_du = fabsf(plain_lnw(K, inv, chi, u + h) - plain_lnw(K, inv, chi, u - h)) / (2.0f * h);
     float e = fabsf(ln_net - ln_p) / fmaxf(dlnw_du, 1e-30f);
     if (!(e == e)) e = 1e30f;
     red[threadIdx.x] = e;
@@ -413,10 +445,11 @@ __global__ void __launch_bounds__(64) calibrate_kernel(const float *__restrict__
 }
 
 // ln w-bar of the plain fitted sampler (training targets without the oracle).
-__global__ void plain_targets_kernel(const float *__restrict__ inv, int64_t n, const float *__restrict__ chi,
-                                     const float *__restrict__ u, float *__restrict__ lnw) {
+__global__ void plain_targets_kernel(const float *__restrict__ inv, const Kind K, int64_t n,
+                                     const float *__restrict__ chi, const float *__restrict__ u,
+                                     float *__restrict__ lnw) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        lnw[i] = plain_lnw(inv, chi[i], u[i]);
+        lnw[i] = plain_lnw(K, inv, chi[i], u[i]);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -513,6 +546,7 @@ struct InferArgs {
     float *xi, *xi_c;
     sfq_counters *counters;
     int *status;              // set to 1 when a bounded wait gave up
+    Kind K;                   // photon: xi, xi_c = 1 - xi; pair: xi = electron share, xi_c = positron share
 };
 
 constexpr uint32_t SM_A = 0, SM_B2 = 16384, SM_B3 = 24576, SM_SMALL = 32768;
@@ -579,13 +613,15 @@ __global__ void __launch_bounds__(IT) infer_tc_kernel(const InferArgs a) {
         const int64_t i = tile * IT + tid;
         const bool valid = i < a.n;
         const float chi = valid ? a.chi[i] : 1.0f;
-        const float u = valid ? a.r[i] : 0.5f;
-        const bool bad = !(chi >= 0.0f) || !(u > 0.0f) || !(u < 1.0f);
-        const bool in_range = chi >= CHI_LO && chi <= CHI_HI;
-        const bool fallback = !bad && (!in_range || fl[cell_of(chi, u)]);
+        const float r = valid ? a.r[i] : 0.5f;
+        const bool bad = !(chi >= 0.0f) || !(r > 0.0f) || !(r < 1.0f);
+        const float rp = 2.0f * r - 1.0f;                 // pair creation: r' (exact for r in (0, 1))
+        const float u = a.K.pair ? fabsf(rp) : r;
+        const bool in_range = chi >= a.K.chi_lo && chi <= a.K.chi_hi;
+        const bool fallback = !bad && (!in_range || fl[cell_of(a.K, chi, u)]);
         // layer 1 on the CUDA cores (binary32 features, bf16-rounded weights)
         float x1, x2;
-        features(in_range ? chi : 1.0f, bad ? 0.5f : u, x1, x2);
+        features(a.K, in_range ? chi : 1.0f, bad ? 0.5f : u, x1, x2);
         float v[H];
 #pragma unroll
         for (int j = 0; j < H; ++j) v[j] = silu(fmaf(w1[2 * j], x1, fmaf(w1[2 * j + 1], x2, b1[j])));
@@ -634,6 +670,18 @@ __global__ void __launch_bounds__(IT) infer_tc_kernel(const InferArgs a) {
                 ++n_nan;
                 xi = 0.0f;
                 xc = 0.0f;
+            } else if (a.K.pair) {
+                bool oor = false;
+                if (fallback) {
+                    pair_shares<float>(a.inv, chi, r, xi, xc, oor);
+                    n_oor += oor;
+                    ++n_fb;
+                } else {
+                    // 1 - v-bar = exp(-u e^y): at most 1 for any network output
+                    const float small = 0.5f * expf(-expf(y + logf(u))), big = 1.0f - small;
+                    xi = rp >= 0.0f ? big : small;
+                    xc = rp >= 0.0f ? small : big;
+                }
             } else {
                 float s;
                 if (fallback) {
@@ -704,17 +752,23 @@ struct DeviceGuard {
 };
 bool a16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
+// The plain fitted sampler the surrogate stands for (training targets, calibration, fallback).
+const float *inv_table(const sfq_mlp *m) {
+    return static_cast<const float *>(m->kind ? m->ctx->d_nbw_inv : m->ctx->d_nlc_inv);
+}
+
 }  // namespace
 
 extern "C" {
 
-sfq_status sfq_mlp_create(sfq_ctx *ctx, uint64_t seed, sfq_mlp **out) {
+static sfq_status mlp_create(sfq_ctx *ctx, uint64_t seed, int kind, sfq_mlp **out) {
     if (!ctx || !out) return SFQ_ERR_ARG;
     *out = nullptr;
     if (ctx->cfg.precision != SFQ_FP32) return fail(ctx, SFQ_ERR_ARG, "the surrogate serves binary32 contexts");
     DeviceGuard g(ctx->device);
     sfq_mlp *m = new sfq_mlp();
     m->ctx = ctx;
+    m->kind = kind;
     float **bufs[4] = {&m->params, &m->m, &m->v, &m->grad};
     cudaError_t e = cudaSuccess;
     for (auto b : bufs)
@@ -736,6 +790,9 @@ sfq_status sfq_mlp_create(sfq_ctx *ctx, uint64_t seed, sfq_mlp **out) {
     *out = m;
     return SFQ_OK;
 }
+
+sfq_status sfq_mlp_create(sfq_ctx *ctx, uint64_t seed, sfq_mlp **out) { return mlp_create(ctx, seed, 0, out); }
+sfq_status sfq_mlp_create_pair(sfq_ctx *ctx, uint64_t seed, sfq_mlp **out) { return mlp_create(ctx, seed, 1, out); }
 
 void sfq_mlp_destroy(sfq_mlp *m) {
     if (!m) return;
@@ -795,7 +852,8 @@ sfq_status sfq_mlp_loss_grad(sfq_mlp *m, int64_t n, const float *chi, const floa
     float *part = nullptr;
     if (e == cudaSuccess) e = cudaMallocAsync(&part, ((size_t)nb * NP + nb) * sizeof(float), s);
     if (e != cudaSuccess) return cuda_fail(m->ctx, e, "sfq_mlp_loss_grad");
-    TrainArgs a{m->params, n, chi, u, lnw, 0, 0, 0, 0, quantize, 2.0f / (float)n, part, part + (size_t)nb * NP};
+    TrainArgs a{m->params, n, chi, u, lnw, 0, 0, 0, 0, quantize, 2.0f / (float)n, part, part + (size_t)nb * NP,
+                kind_of(m->kind)};
     train_kernel<<<nb, TB, sizeof(TrainSmem), s>>>(a);
     reduce_kernel<<<(NP + 255) / 256, 256, 0, s>>>(part, part + (size_t)nb * NP, nb, grad, loss, 1.0f / (float)n);
     e = cudaGetLastError();
@@ -819,7 +877,7 @@ sfq_status sfq_mlp_train(sfq_mlp *m, int64_t n, const float *chi, const float *u
     if (e != cudaSuccess) return cuda_fail(m->ctx, e, "sfq_mlp_train");
     for (int64_t t = 0; t < steps && e == cudaSuccess; ++t) {
         TrainArgs a{m->params, n, chi, u, lnw, 0, 1, seed, (uint32_t)(m->adam_t + 1), quantize,
-                    2.0f / (float)batch, part, part + (size_t)nb * NP};
+                    2.0f / (float)batch, part, part + (size_t)nb * NP, kind_of(m->kind)};
         train_kernel<<<nb, TB, sizeof(TrainSmem), s>>>(a);
         reduce_kernel<<<(NP + 255) / 256, 256, 0, s>>>(part, part + (size_t)nb * NP, nb, m->grad,
                                                         loss_history ? loss_history + t : nullptr,
@@ -844,7 +902,7 @@ sfq_status sfq_mlp_predict_lnw(sfq_mlp *m, int64_t n, const float *chi, const fl
     DeviceGuard g(m->ctx->device);
     const int64_t blocks = (n + 127) / 128;
     const int grid = (int)(blocks < (int64_t)m->ctx->num_sms * 8 ? blocks : (int64_t)m->ctx->num_sms * 8);
-    predict_kernel<<<grid, 128, 0, (cudaStream_t)stream>>>(m->params, n, chi, u, lnw);
+    predict_kernel<<<grid, 128, 0, (cudaStream_t)stream>>>(m->params, kind_of(m->kind), n, chi, u, lnw);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SFQ_OK : cuda_fail(m->ctx, e, "sfq_mlp_predict_lnw");
 }
@@ -857,8 +915,7 @@ sfq_status sfq_mlp_plain_targets(sfq_mlp *m, int64_t n, const float *chi, const 
     DeviceGuard g(m->ctx->device);
     const int64_t blocks = (n + 255) / 256;
     const int grid = (int)(blocks < (int64_t)m->ctx->num_sms * 8 ? blocks : (int64_t)m->ctx->num_sms * 8);
-    plain_targets_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(static_cast<const float *>(m->ctx->d_nlc_inv), n,
-                                                                 chi, u, lnw);
+    plain_targets_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(inv_table(m), kind_of(m->kind), n, chi, u, lnw);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SFQ_OK : cuda_fail(m->ctx, e, "sfq_mlp_plain_targets");
 }
@@ -868,8 +925,7 @@ sfq_status sfq_mlp_calibrate(sfq_mlp *m, float tol_u, int32_t *n_flagged, float 
     if (!(tol_u > 0.0f)) return fail(m->ctx, SFQ_ERR_ARG, "tol_u must be positive");
     DeviceGuard g(m->ctx->device);
     const cudaStream_t s = (cudaStream_t)stream;
-    calibrate_kernel<<<NCELL, 64, 0, s>>>(m->params, static_cast<const float *>(m->ctx->d_nlc_inv), tol_u, m->flags,
-                                          m->cell_err);
+    calibrate_kernel<<<NCELL, 64, 0, s>>>(m->params, kind_of(m->kind), inv_table(m), tol_u, m->flags, m->cell_err);
     cudaError_t e = cudaGetLastError();
     std::vector<uint8_t> f(NCELL);
     std::vector<float> ce(NCELL);
@@ -889,8 +945,8 @@ sfq_status sfq_mlp_calibrate(sfq_mlp *m, float tol_u, int32_t *n_flagged, float 
     return SFQ_OK;
 }
 
-sfq_status sfq_mlp_sample_photon_xi(sfq_mlp *m, int64_t n, const void *chi, const void *r, void *xi, void *xi_c,
-                                    int32_t use_flags, sfq_counters *counters, void *stream) {
+static sfq_status mlp_sample(sfq_mlp *m, int64_t n, const void *chi, const void *r, void *xi, void *xi_c,
+                             int32_t use_flags, sfq_counters *counters, void *stream) {
     if (!m) return SFQ_ERR_ARG;
     if (n < 0) return fail(m->ctx, SFQ_ERR_ARG, "n < 0");
     if (n == 0) return SFQ_OK;
@@ -913,12 +969,24 @@ sfq_status sfq_mlp_sample_photon_xi(sfq_mlp *m, int64_t n, const void *chi, cons
     const int64_t ntiles = (n + IT - 1) / IT;
     int64_t grid = (int64_t)per_sm * m->ctx->num_sms;
     if (ntiles < grid) grid = ntiles;
-    InferArgs a{m->params, use_flags ? m->flags : nullptr, static_cast<const float *>(m->ctx->d_nlc_inv), n,
+    InferArgs a{m->params, use_flags ? m->flags : nullptr, inv_table(m), n,
                 static_cast<const float *>(chi), static_cast<const float *>(r), static_cast<float *>(xi),
-                static_cast<float *>(xi_c), counters, nullptr};
+                static_cast<float *>(xi_c), counters, nullptr, kind_of(m->kind)};
     infer_tc_kernel<<<(unsigned)grid, IT, INFER_SMEM, (cudaStream_t)stream>>>(a);
     e = cudaGetLastError();
-    return e == cudaSuccess ? SFQ_OK : cuda_fail(m->ctx, e, "sfq_mlp_sample_photon_xi");
+    return e == cudaSuccess ? SFQ_OK : cuda_fail(m->ctx, e, "sfq_mlp_sample_*_xi");
+}
+
+sfq_status sfq_mlp_sample_photon_xi(sfq_mlp *m, int64_t n, const void *chi, const void *r, void *xi, void *xi_c,
+                                    int32_t use_flags, sfq_counters *counters, void *stream) {
+    if (m && m->kind != 0) return fail(m->ctx, SFQ_ERR_ARG, "a pair-creation surrogate: use sfq_mlp_sample_pair_xi");
+    return mlp_sample(m, n, chi, r, xi, xi_c, use_flags, counters, stream);
+}
+
+sfq_status sfq_mlp_sample_pair_xi(sfq_mlp *m, int64_t n, const void *chi, const void *r, void *xi_e, void *xi_p,
+                                  int32_t use_flags, sfq_counters *counters, void *stream) {
+    if (m && m->kind != 1) return fail(m->ctx, SFQ_ERR_ARG, "a photon-emission surrogate: use sfq_mlp_sample_photon_xi");
+    return mlp_sample(m, n, chi, r, xi_e, xi_p, use_flags, counters, stream);
 }
 
 }  // extern "C"

@@ -54,6 +54,11 @@ std::string graph_key(const sfq_ctx *ctx, const sfq_particles *p, const sfq_fiel
     k.append(reinterpret_cast<const char *>(&step0), sizeof(step0));
     k.append(reinterpret_cast<const char *>(&nsteps), sizeof(nsteps));
     k.append(reinterpret_cast<const char *>(shape), sizeof(shape));
+    // options baked into the recorded kernel arguments
+    const double cut = ctx->pair_chi_min;
+    const void *inv_r[3] = {ctx->d_nlc_inv_r, ctx->d_nbw_inv_r, reinterpret_cast<const void *>((intptr_t)ctx->inv_tr)};
+    k.append(reinterpret_cast<const char *>(&cut), sizeof(cut));
+    k.append(reinterpret_cast<const char *>(inv_r), sizeof(inv_r));
     return k;
 }
 

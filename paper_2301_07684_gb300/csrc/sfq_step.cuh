@@ -57,6 +57,7 @@ struct StepArgs {
     T inv_rho;       // 1 / rho
     T rho;
     T inv_dt, inv_dt2;
+    T pair_chi_min;  // NBW rate is zero below this chi (0.01, or the "fast" cutoff)
     Tables<T> tab;
     sfq_counters *counters;
 };
@@ -294,7 +295,7 @@ __device__ __forceinline__ void reserve_records(unsigned long long *ocount, unsi
 // global atomic per batch, before the sampling when every record count is known up
 // front (no beyond-LCFA lane, whose emission may be rejected), so that the atomic's
 // latency overlaps the sampling.
-template <typename T>
+template <typename T, bool TRUNC = false>
 __device__ __forceinline__ void process_events_core(const StepArgs<T> &a, uint32_t step, int64_t ei, T eg, T echi,
                                                     T e_aux, T px, T py, T pz, uint8_t fl, bool valid, Cnt &c,
                                                     EvOut<T> &o) {
@@ -317,16 +318,16 @@ __device__ __forceinline__ void process_events_core(const StepArgs<T> &a, uint32
         const T r1 = uniform<T>(w.w[1]);
         if (photon) {
             ++c.v[C_EV];
-            pair_shares<T>(a.tab.nbw_inv, echi, r1, xa, xb, oor);
+            pair_shares_sel<T, TRUNC>(a.tab, echi, r1, xa, xb, oor);
             ++c.v[C_PAIR];
         } else if (e_aux < (T)0) {
             ++c.v[C_EV];
-            xa = photon_s<T>(a.tab.nlc_inv, echi, r1, oor);      // s
+            xa = photon_s_sel<T, TRUNC>(a.tab, echi, r1, oor);      // s
             xb = uniform<T>(w.w[0]);                               // for the fresh optical depth
             ++c.v[C_EMIT];
         } else {
             // beyond-LCFA: LCFA sample, then the rejection of Eq. rej_cond below gamma_LCFA
-            xa = photon_s<T>(a.tab.nlc_inv, echi, r1, oor);
+            xa = photon_s_sel<T, TRUNC>(a.tab, echi, r1, oor);
             xb = (T)-1;                                            // marks: no optical depth
             bool accept = true;
             const T gbar = eg * xa / ((T)1 + xa);
@@ -419,11 +420,11 @@ __device__ __forceinline__ void process_events_core(const StepArgs<T> &a, uint32
 
 // process_events_core at the launch's step with the parent's new state stored to the
 // population in global memory.
-template <typename T>
+template <typename T, bool TRUNC = false>
 __device__ __forceinline__ void process_events(const StepArgs<T> &a, int64_t ei, T eg, T echi, T e_aux, T px,
                                                T py, T pz, uint8_t fl, bool valid, Cnt &c) {
     EvOut<T> o;
-    process_events_core<T>(a, a.step, ei, eg, echi, e_aux, px, py, pz, fl, valid, c, o);
+    process_events_core<T, TRUNC>(a, a.step, ei, eg, echi, e_aux, px, py, pz, fl, valid, c, o);
     if (o.what & 1) { a.px[ei] = o.px; a.py[ei] = o.py; a.pz[ei] = o.pz; }
     if (o.what & 2) a.tau[ei] = o.tau;
     if (o.what & 4) a.flags[ei] = o.fl;
@@ -450,7 +451,7 @@ __device__ __forceinline__ bool step_particle(const StepArgs<T> &a, const T *s_n
         ++c.v[C_NAN];
         d = (T)0;
     } else if (photon) {
-        d = a.prefdt * wtilde_pair<T>(s_nbw, chi, oor) * inv_g;
+        d = a.prefdt * wtilde_pair<T>(s_nbw, chi, oor, a.pair_chi_min) * inv_g;
     } else {
         d = a.prefdt * (chi * inv_g) * wtilde_rad<T>(s_nlc, chi, oor);
     }
@@ -481,7 +482,7 @@ __device__ __forceinline__ bool step_particle_v(const StepArgs<T> &a, const T *s
         ++c.v[C_NAN];
         d = (T)0;
     } else if (photon) {
-        d = a.prefdt * wtilde_pair<T>(s_nbw, chi, oor) * inv_g;
+        d = a.prefdt * wtilde_pair<T>(s_nbw, chi, oor, a.pair_chi_min) * inv_g;
     } else {
         d = a.prefdt * (chi * inv_g) * wtilde_rad<T>(s_nlc, chi, oor);
     }
@@ -495,7 +496,7 @@ __device__ __forceinline__ bool step_particle_v(const StepArgs<T> &a, const T *s
 // Each warp streams chunks of 32*PPT particles and compacts event lanes into a
 // warp-private ring in shared memory; a full batch of 32 events is sampled by the
 // whole warp.  No block-wide barrier inside the loop.
-template <typename T, int FK, int PPT>
+template <typename T, int FK, int PPT, bool TRUNC = false>
 __global__ void __launch_bounds__(STEP_BS, SFQ_STEP_MINB) mc_step_kernel(const StepArgs<T> a) {
     using Q = L<T>;
     constexpr int WARPS = STEP_BS / 32;
@@ -558,7 +559,8 @@ __global__ void __launch_bounds__(STEP_BS, SFQ_STEP_MINB) mc_step_kernel(const S
             const QEntryX<T> e = q[(head + lane) & (QS - 1)];
             __syncwarp();
             head += 32;
-            process_events<T>(a, e.i, e.g, e.chi, e.aux, a.px[e.i], a.py[e.i], a.pz[e.i], a.flags[e.i], true, c);
+            process_events<T, TRUNC>(a, e.i, e.g, e.chi, e.aux, a.px[e.i], a.py[e.i], a.pz[e.i], a.flags[e.i], true,
+                                     c);
         }
     }
     // drain the partial batch
@@ -567,7 +569,7 @@ __global__ void __launch_bounds__(STEP_BS, SFQ_STEP_MINB) mc_step_kernel(const S
         const unsigned nv = tail - head;
         const QEntryX<T> e = q[(head + lane) & (QS - 1)];
         const bool v = (unsigned)lane < nv;
-        process_events<T>(a, e.i, e.g, e.chi, e.aux, v ? a.px[e.i] : (T)0, v ? a.py[e.i] : (T)0,
+        process_events<T, TRUNC>(a, e.i, e.g, e.chi, e.aux, v ? a.px[e.i] : (T)0, v ? a.py[e.i] : (T)0,
                           v ? a.pz[e.i] : (T)0, v ? a.flags[e.i] : (uint8_t)0, v, c);
     }
     flush_counters(c, a.counters);

@@ -95,7 +95,7 @@ __device__ __forceinline__ void raise_timeout(sfq_counters *c) {
     if (c) atomicAdd(&c->timeouts, 1ull);
 }
 
-template <typename T, int FK, int CW>
+template <typename T, int FK, int CW, bool TRUNC = false>
 __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const StepArgs<T> a) {
     using Q = L<T>;
     using S = TmaStage<T, FK, CW>;
@@ -340,14 +340,15 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
             const QEntry<T> e = q[(head + lane) & (QS - 1)];
             __syncwarp();
             head += 32;
-            process_events<T>(a, e.i, e.g, e.chi, (T)-1, e.px, e.py, e.pz, (uint8_t)e.fl, true, c);
+            process_events<T, TRUNC>(a, e.i, e.g, e.chi, (T)-1, e.px, e.py, e.pz, (uint8_t)e.fl, true, c);
         }
     }
     __syncwarp();
     if (tail != head) {
         const unsigned nv = tail - head;
         const QEntry<T> e = q[(head + lane) & (QS - 1)];
-        process_events<T>(a, e.i, e.g, e.chi, (T)-1, e.px, e.py, e.pz, (uint8_t)e.fl, (unsigned)lane < nv, c);
+        process_events<T, TRUNC>(a, e.i, e.g, e.chi, (T)-1, e.px, e.py, e.pz, (uint8_t)e.fl, (unsigned)lane < nv,
+                                 c);
     }
     // counters of the consumer warps (the producer warp has returned)
     if (a.counters) {

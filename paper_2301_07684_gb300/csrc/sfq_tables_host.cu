@@ -1,5 +1,8 @@
 // Host copies of the fitted tables (generated by fitgen/generate.py), uploaded to the
 // device by sfq_init.
+#include <cstring>
+#include <vector>
+
 #include "sfq_internal.h"
 #include "sfq_tables_layout.h"
 #include "sfq_tables.inc"
@@ -24,4 +27,94 @@ HostTables host_tables(int precision) {
     }
     return t;
 }
+
+int inv_coefficients(int precision) {
+    static_assert(NLC_INV_F32_DX == NLC_INV_F32_DY && NBW_INV_F32_DX == NLC_INV_F32_DX &&
+                      NBW_INV_F32_DY == NLC_INV_F32_DY, "square binary32 inverse-CDF pieces");
+    static_assert(NLC_INV_F64_DX == NLC_INV_F64_DY && NBW_INV_F64_DX == NLC_INV_F64_DX &&
+                      NBW_INV_F64_DY == NLC_INV_F64_DY, "square binary64 inverse-CDF pieces");
+    return precision == SFQ_FP64 ? NLC_INV_F64_DX + 1 : NLC_INV_F32_DX + 1;
+}
+
+namespace {
+
+// Monomial <-> Chebyshev bases of degree < n on [-1, 1] (row-major n x n):
+//   c2m[a n + k]: coefficient of x^k in T_a (T_0 = 1, T_1 = x, T_{a+1} = 2x T_a - T_{a-1});
+//   m2c[k n + a]: coefficient of T_a in x^k (x T_0 = T_1, x T_a = (T_{a+1} + T_{a-1})/2).
+void cheb_bases(int n, std::vector<double> &c2m, std::vector<double> &m2c) {
+    c2m.assign((size_t)n * n, 0.0);
+    m2c.assign((size_t)n * n, 0.0);
+    c2m[0] = 1.0;
+    if (n > 1) c2m[n + 1] = 1.0;
+    for (int a = 1; a + 1 < n; ++a)
+        for (int k = 0; k < n; ++k)
+            c2m[(a + 1) * n + k] = (k > 0 ? 2.0 * c2m[a * n + k - 1] : 0.0) - c2m[(a - 1) * n + k];
+    m2c[0] = 1.0;
+    for (int k = 0; k + 1 < n; ++k)
+        for (int a = 0; a < n; ++a) {
+            const double v = m2c[k * n + a];
+            if (v == 0.0) continue;
+            if (a == 0) {
+                m2c[(k + 1) * n + 1] += v;
+            } else {
+                if (a + 1 < n) m2c[(k + 1) * n + a + 1] += 0.5 * v;
+                m2c[(k + 1) * n + a - 1] += 0.5 * v;
+            }
+        }
+}
+
+template <typename T>
+std::vector<unsigned char> truncate_pieces(const T *src, size_t count, int n, int tr) {
+    const int m = n - tr;                                   // kept coefficients per variable
+    const int row = (m * (int)sizeof(T) + 15) / 16 * 16 / (int)sizeof(T);
+    const size_t pieces = count / ((size_t)n * n);
+    std::vector<double> c2m, m2c;
+    cheb_bases(n, c2m, m2c);
+    std::vector<unsigned char> out(pieces * (size_t)m * row * sizeof(T), 0);
+    T *dst = reinterpret_cast<T *>(out.data());
+    std::vector<double> C((size_t)n * n), Q((size_t)n * n);
+    for (size_t p = 0; p < pieces; ++p) {
+        const T *P = src + p * (size_t)n * n;               // P[i n + j]: x^i y^j
+        // C = M P M^T in the Chebyshev basis, M[a][i] = m2c[i][a]
+        for (int a = 0; a < n; ++a)
+            for (int j = 0; j < n; ++j) {
+                double acc = 0.0;
+                for (int i = 0; i < n; ++i) acc += m2c[i * n + a] * (double)P[i * n + j];
+                Q[a * n + j] = acc;
+            }
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b < n; ++b) {
+                double acc = 0.0;
+                for (int j = 0; j < n; ++j) acc += Q[a * n + j] * m2c[j * n + b];
+                C[a * n + b] = acc;
+            }
+        // keep T_a(x) T_b(y) with a, b < m and return to monomials: P' = N C' N^T, N[i][a] = c2m[a][i]
+        for (int i = 0; i < m; ++i)
+            for (int b = 0; b < m; ++b) {
+                double acc = 0.0;
+                for (int a = 0; a < m; ++a) acc += c2m[a * n + i] * C[a * n + b];
+                Q[i * n + b] = acc;
+            }
+        T *D = dst + p * (size_t)m * row;
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) {
+                double acc = 0.0;
+                for (int b = 0; b < m; ++b) acc += Q[i * n + b] * c2m[b * n + j];
+                D[i * row + j] = (T)acc;
+            }
+    }
+    return out;
+}
+
+}  // namespace
+
+std::vector<unsigned char> truncated_inv_table(int precision, bool pair, int tr) {
+    const int n = inv_coefficients(precision);
+    if (precision == SFQ_FP64)
+        return pair ? truncate_pieces(nbw_inv_f64, sizeof(nbw_inv_f64) / sizeof(double), n, tr)
+                    : truncate_pieces(nlc_inv_f64, sizeof(nlc_inv_f64) / sizeof(double), n, tr);
+    return pair ? truncate_pieces(nbw_inv_f32, sizeof(nbw_inv_f32) / sizeof(float), n, tr)
+                : truncate_pieces(nlc_inv_f32, sizeof(nlc_inv_f32) / sizeof(float), n, tr);
+}
+
 }  // namespace sfq

@@ -93,6 +93,12 @@ def lib():
         L.sfq_mc_run_fused.argtypes = [vp, C.POINTER(Particles), C.POINTER(Fields), C.c_uint32, C.c_uint32,
                                        C.POINTER(Products), vp, vp]
         L.sfq_mc_run_fused.restype = st
+        L.sfq_set_pair_rate_cutoff.argtypes = [vp, C.c_double]
+        L.sfq_set_pair_rate_cutoff.restype = st
+        L.sfq_set_sampler_coefficients.argtypes = [vp, C.c_int32]
+        L.sfq_set_sampler_coefficients.restype = st
+        L.sfq_sampler_coefficients.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        L.sfq_sampler_coefficients.restype = st
         L.sfq_autotune_step.argtypes = [vp, C.POINTER(Particles), C.POINTER(Fields), u32, i64,
                                         C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_double), vp]
         L.sfq_autotune_step.restype = st
@@ -121,6 +127,10 @@ def lib():
         L.sfq_mlp_calibrate.argtypes = [vp, C.c_float, C.POINTER(C.c_int32), C.POINTER(C.c_float), vp]
         L.sfq_mlp_calibrate.restype = st
         L.sfq_mlp_sample_photon_xi.argtypes = [vp, i64, vp, vp, vp, vp, C.c_int32, vp, vp]
+        L.sfq_mlp_create_pair.argtypes = [vp, C.c_uint64, C.POINTER(vp)]
+        L.sfq_mlp_create_pair.restype = st
+        L.sfq_mlp_sample_pair_xi.argtypes = [vp, i64, vp, vp, vp, vp, C.c_int32, vp, vp]
+        L.sfq_mlp_sample_pair_xi.restype = st
         L.sfq_mlp_sample_photon_xi.restype = st
         L.sfq_set_step_shape.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
         L.sfq_set_step_shape.restype = st
@@ -131,10 +141,11 @@ def lib():
 
 EXPORTED = ["sfq_init", "sfq_finalize", "sfq_last_error", "sfq_constants", "sfq_photon_rate", "sfq_pair_rate",
             "sfq_uniforms", "sfq_sample_photon_xi", "sfq_sample_pair_xi", "sfq_mc_step", "sfq_mc_run",
-            "sfq_mc_run_fused", "sfq_autotune_step", "sfq_sort_scratch_bytes", "sfq_sort_products", "sfq_sort_products_noalloc", "sfq_set_step_shape",
+            "sfq_mc_run_fused", "sfq_set_pair_rate_cutoff", "sfq_set_sampler_coefficients",
+            "sfq_sampler_coefficients", "sfq_autotune_step", "sfq_sort_scratch_bytes", "sfq_sort_products", "sfq_sort_products_noalloc", "sfq_set_step_shape",
             "sfq_mlp_num_params", "sfq_mlp_create", "sfq_mlp_destroy", "sfq_mlp_get_params", "sfq_mlp_set_params",
             "sfq_mlp_loss_grad", "sfq_mlp_train", "sfq_mlp_predict_lnw", "sfq_mlp_plain_targets", "sfq_mlp_calibrate",
-            "sfq_mlp_sample_photon_xi",
+            "sfq_mlp_sample_photon_xi", "sfq_mlp_create_pair", "sfq_mlp_sample_pair_xi",
             "sfq_version"]
 
 
@@ -272,6 +283,20 @@ class Context:
         self._check(lib().sfq_mc_run_fused(self._h, C.byref(P), C.byref(F), step0, nsteps, C.byref(O),
                                            _ptr(counters), _stream()), "sfq_mc_run_fused")
 
+    def set_pair_rate_cutoff(self, chi_min: float):
+        """NBW rate zero below chi_min (0.01 by default; 0.3 gives the paper's "fast" rate)."""
+        self._check(lib().sfq_set_pair_rate_cutoff(self._h, float(chi_min)), "sfq_set_pair_rate_cutoff")
+
+    def set_sampler_coefficients(self, k: int):
+        """Use the leading k x k Chebyshev coefficients of each inverse-CDF piece (k = n, n-1, n-2)."""
+        self._check(lib().sfq_set_sampler_coefficients(self._h, int(k)), "sfq_set_sampler_coefficients")
+
+    def sampler_coefficients(self):
+        """(n, k): coefficients per variable of the tables and those in use."""
+        n, k = C.c_int32(0), C.c_int32(0)
+        self._check(lib().sfq_sampler_coefficients(self._h, C.byref(n), C.byref(k)), "sfq_sampler_coefficients")
+        return n.value, k.value
+
     def autotune_step(self, particles: "ParticleBuffers", fields: "FieldSource", step=0, sample_n=0):
         """Times every launch shape on a copy of the population; returns (variant, shape, ms)."""
         P, F = particles.descriptor(), fields.descriptor()
@@ -303,12 +328,20 @@ SORT_NOALLOC_SCRATCH_BYTES = 44 << 20
 
 
 class Surrogate:
-    """The learned inverse-CDF surrogate (sfq_mlp_*) of one binary32 context."""
+    """The learned inverse-CDF surrogate (sfq_mlp_*) of one binary32 context: kind "photon"
+    (Eq. again; input u = r, output ln w-bar) or "pair" (Eq. again_pp; input u = |2r - 1|,
+    output ln y, y = 1 - v-bar)."""
 
-    def __init__(self, ctx: Context, seed=0):
+    def __init__(self, ctx: Context, seed=0, kind="photon"):
         self.ctx = ctx
+        self.kind = kind
         h = C.c_void_p()
-        ctx._check(lib().sfq_mlp_create(ctx._h, seed, C.byref(h)), "sfq_mlp_create")
+        if kind == "pair":
+            ctx._check(lib().sfq_mlp_create_pair(ctx._h, seed, C.byref(h)), "sfq_mlp_create_pair")
+        elif kind == "photon":
+            ctx._check(lib().sfq_mlp_create(ctx._h, seed, C.byref(h)), "sfq_mlp_create")
+        else:
+            raise SfqError(f"unknown surrogate kind {kind!r}")
         self._h = h
 
     def close(self):
@@ -376,6 +409,15 @@ class Surrogate:
                                                        int(use_flags), _ptr(counters), _stream()),
                         "sfq_mlp_sample_photon_xi")
         return xi, xc
+
+    def sample_pair_xi(self, chi, r, use_flags=True, counters=None):
+        """Electron and positron energy shares for uniforms r (kind "pair")."""
+        xe = torch.empty_like(chi)
+        xp = torch.empty_like(chi)
+        self.ctx._check(lib().sfq_mlp_sample_pair_xi(self._h, chi.numel(), _ptr(chi), _ptr(r), _ptr(xe), _ptr(xp),
+                                                     int(use_flags), _ptr(counters), _stream()),
+                        "sfq_mlp_sample_pair_xi")
+        return xe, xp
 
 
 def sort_scratch_bytes(n):

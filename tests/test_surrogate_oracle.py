@@ -94,3 +94,38 @@ def test_bf16_rounding_matches_torch(S):
     x32 = x.astype(np.float32)
     ref = torch.tensor(x32).to(torch.bfloat16).to(torch.float64).numpy()
     assert np.array_equal(S.bf16(x32), ref)
+
+
+@pytest.fixture(scope="module")
+def coarse_pair(S):
+    return S.DensePairCDF(ds=0.1, dx=0.2)
+
+
+def test_dense_pair_cdf_matches_brent(S, coarse_pair):
+    """The pair-share CDF table (logit of I~_pp over its complement, Eq. tilde_I_pp) against
+    the oracle's Brent roots of Eq. again_pp: the CDF at the root returns |r'|, and the
+    table's inverse returns the root."""
+    from oracle import oracle as O
+    g = np.random.default_rng(7)
+    m = 200
+    chi = np.exp(g.uniform(np.log(0.1), np.log(100.0), m))
+    a = g.uniform(2.0 ** -24, 1.0 - 2.0 ** -24, m)
+    v, y = O.pair_vbar(a, chi)
+    at = coarse_pair.cdf_y(chi, y)
+    assert np.max(np.abs(at - a)) < 5e-6
+    assert np.max(np.abs((1.0 - at) - (1.0 - a)) / (1.0 - a)) < 1e-4
+    yt = np.exp(coarse_pair.inverse_lny(chi, a))
+    assert np.max(np.abs(yt / y - 1.0)) < 1e-4
+    # shares built from the root: the PIT returns |r'|
+    xe, xp = 1.0 - 0.5 * y, 0.5 * y
+    assert np.max(np.abs(coarse_pair.pit(chi, xe, xp) - a)) < 5e-6
+    # the two halves are independent integrals that add up to W~_pair
+    lo, up = O.itilde_pp_batch(v, chi), O.itilde_pp_upper_y_batch(y, chi)
+    assert np.max(np.abs((lo + up) / O.wtilde_pair(chi) - 1.0)) < 1e-10
+
+
+def test_pair_kind_features(S):
+    """The pair kind maps chi in [0.1, 100] onto [-1, 1] and u = |r'| as the photon kind maps u."""
+    x = S.features(np.log([0.1, 100.0]), [0.5, 0.5], kind="pair")
+    assert np.allclose(x[:, 0], [-1.0, 1.0], atol=1e-15)
+    assert np.allclose(x[:, 1], S.features([0.0, 0.0], [0.5, 0.5])[:, 1])
