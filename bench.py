@@ -623,7 +623,7 @@ def main():
     # ncu capture summarised in profiles/mc_step_tma_fp32_soa_4M.md (4,194,304 particles;
     # the per-particle streams scale in proportion to n).  Re-measure whenever that kernel
     # changes, and pass --traffic-per-update 0 to report null meanwhile.
-    ap.add_argument("--traffic-per-update", type=float, default=51.87,
+    ap.add_argument("--traffic-per-update", type=float, default=51.81,
                     help="DRAM bytes per update of the step kernel from an ncu capture (for roofline.traffic)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
