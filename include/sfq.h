@@ -247,6 +247,17 @@ sfq_status sfq_mc_run(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f,
 sfq_status sfq_mc_run_fused(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, uint32_t step0,
                             uint32_t nsteps, const sfq_products *out, sfq_counters *counters, void *stream);
 
+/* One Boris push of the momenta (Boris 1970), the particle pusher a PIC code runs between
+ * Monte Carlo steps; the paper's library leaves it to the host code.  For every alive
+ * electron (charge -1) and positron (+1) of `p`, in the fields `f` at `step` (as
+ * sfq_mc_step reads them): u- = u + q E dt/2, t = q B dt / (2 gamma(u-)),
+ * s = 2 t / (1 + t.t), u+ = u- + (u- + u- x t) x s, u = u+ + q E dt/2, in the normalised
+ * units of the step (u = p / m c, fields in E_r, dt in 1/omega_r).  Photons and dead
+ * particles are left unchanged; positions are not tracked.  dt must be positive and finite,
+ * buffers as for sfq_mc_step, else SFQ_ERR_ARG.  Asynchronous on `stream`. */
+sfq_status sfq_push(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, uint32_t step, double dt,
+                    void *stream);
+
 /* Options of a context.  Both are read when work is enqueued; a CUDA graph recorded by
  * sfq_mc_run keeps the options it was recorded with, and a later call with other options
  * records a new graph.

@@ -280,6 +280,17 @@ def itilde_pp_upper_y_batch(y, chi):
     return out
 
 
+def boris_push(u, E, B, q, dt):
+    """Boris push of momenta u (n x 3) in fields E, B (n x 3) for charges q (n; in |e|, 0 for
+    photons), normalised units; returns the new momenta."""
+    u = np.ascontiguousarray(np.array(u, np.float64).reshape(-1, 3))
+    E = np.ascontiguousarray(np.broadcast_to(np.asarray(E, np.float64), u.shape))
+    B = np.ascontiguousarray(np.broadcast_to(np.asarray(B, np.float64), u.shape))
+    q = np.ascontiguousarray(np.broadcast_to(np.asarray(q, np.float64), (u.shape[0],)))
+    lib().orc_batch_boris_push(_I64(u.shape[0]), _p(u), _p(E), _p(B), _p(q), _D(dt))
+    return u
+
+
 def philox(ids, step, tag, seed):
     ids = np.ascontiguousarray(np.asarray(ids, dtype=np.uint64))
     out = np.empty((ids.size, 4), dtype=np.uint32)

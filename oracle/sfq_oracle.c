@@ -578,6 +578,39 @@ void orc_batch_itilde_pp_upper_y(int64_t n, const double *y, const double *chi, 
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t i = 0; i < n; ++i) out[i] = orc_itilde_pp_upper_y(y[i], chi[i]);
 }
+/* ------------------------------------------------------------------------- */
+/* Boris push of the momentum (the pusher a PIC code runs between Monte Carlo */
+/* steps; Boris 1970, in the normalised units of the step: du/dt = q (E + u x */
+/* B / gamma), u = p / m c, fields in E_r, time in 1/omega_r):               */
+/*   u- = u + q E dt/2;  t = q B dt / (2 gamma(u-));  s = 2 t / (1 + t.t);    */
+/*   u' = u- + u- x t;  u+ = u- + u' x s;  u_new = u+ + q E dt/2.             */
+/* ------------------------------------------------------------------------- */
+static void cross3(const double a[3], const double b[3], double c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+void orc_boris_push(double u[3], const double E[3], const double B[3], double q, double dt) {
+    double um[3], t[3], s[3], c[3], up[3];
+    for (int k = 0; k < 3; ++k) um[k] = u[k] + 0.5 * q * dt * E[k];
+    const double gm = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+    for (int k = 0; k < 3; ++k) t[k] = 0.5 * q * dt * B[k] / gm;
+    const double tt = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    for (int k = 0; k < 3; ++k) s[k] = 2.0 * t[k] / (1.0 + tt);
+    cross3(um, t, c);
+    double uprime[3];
+    for (int k = 0; k < 3; ++k) uprime[k] = um[k] + c[k];
+    cross3(uprime, s, c);
+    for (int k = 0; k < 3; ++k) up[k] = um[k] + c[k];
+    for (int k = 0; k < 3; ++k) u[k] = up[k] + 0.5 * q * dt * E[k];
+}
+/* n particles: u (n x 3, in/out), E, B (n x 3), q (n; 0 leaves u unchanged). */
+void orc_batch_boris_push(int64_t n, double *u, const double *E, const double *B, const double *q, double dt) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i)
+        if (q[i] != 0.0) orc_boris_push(u + 3 * i, E + 3 * i, B + 3 * i, q[i], dt);
+}
+
 void orc_batch_philox(int64_t n, const uint64_t *id, uint32_t step, uint32_t tag, uint64_t seed,
                       uint32_t *out4) {
     const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};

@@ -297,6 +297,22 @@ sfq_status sfq_mc_run_fused(sfq_ctx *ctx, const sfq_particles *p, const sfq_fiel
     return e == cudaSuccess ? SFQ_OK : cuda_fail(ctx, e, "sfq_mc_run_fused");
 }
 
+sfq_status sfq_push(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, uint32_t step, double dt,
+                    void *stream) {
+    if (!ctx) return SFQ_ERR_ARG;
+    sfq_products none{};
+    unsigned long long *dummy = nullptr;
+    none.count = reinterpret_cast<unsigned long long *>(&dummy);   // only validated, never written
+    const sfq_status st = sfq::validate_step(ctx, p, f, &none, nullptr, nullptr);
+    if (st != SFQ_OK) return st;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, SFQ_ERR_ARG, "dt must be positive and finite");
+    if (p->n == 0) return SFQ_OK;
+    DeviceGuard g(ctx->device);
+    sfq::StepLaunch L{ctx, p, f, step, &none, nullptr, nullptr, (cudaStream_t)stream, 0, 0, 0};
+    const cudaError_t e = ctx->cfg.precision == SFQ_FP64 ? sfq::launch_push_f64(L, dt) : sfq::launch_push_f32(L, dt);
+    return e == cudaSuccess ? SFQ_OK : cuda_fail(ctx, e, "sfq_push");
+}
+
 sfq_status sfq_set_pair_rate_cutoff(sfq_ctx *ctx, double chi_min) {
     if (!ctx) return SFQ_ERR_ARG;
     if (!(chi_min >= 0.01) || !(chi_min <= 2000.0))

@@ -74,6 +74,8 @@ cudaError_t launch_uniforms_f64(int64_t n, const uint64_t *id, uint32_t step, ui
 cudaError_t launch_step_f32(const StepLaunch &);
 cudaError_t launch_step_f64(const StepLaunch &);
 cudaError_t launch_fused_f32(const StepLaunch &, uint32_t nsteps);
+cudaError_t launch_push_f32(const StepLaunch &, double dt);
+cudaError_t launch_push_f64(const StepLaunch &, double dt);
 // the same with the truncated samplers compiled in (sfq_launch_tr_f32.cu / _f64.cu)
 cudaError_t launch_step_trunc_f32(const StepLaunch &);
 cudaError_t launch_step_trunc_f64(const StepLaunch &);

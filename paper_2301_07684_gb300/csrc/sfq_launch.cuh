@@ -3,6 +3,7 @@
 #pragma once
 #include "sfq_internal.h"
 #include "sfq_fused.cuh"
+#include "sfq_push.cuh"
 #include "sfq_step_tma.cuh"
 
 namespace sfq {
@@ -260,6 +261,20 @@ static cudaError_t launch_fused_t(const StepLaunch &L, uint32_t nsteps) {
     const uint32_t kstep = f.k_step % K;
     const uint32_t off0 = (uint32_t)(((uint64_t)L.step * (uint64_t)f.k_step) % (uint64_t)K);
     kern<<<grid, FUSED_BS, smem, L.stream>>>(a, L.step, nsteps, off0, kstep);
+    return cudaGetLastError();
+}
+
+// One Boris push of the population at L.step (sfq_push.cuh).
+template <typename T>
+static cudaError_t launch_push_t(const StepLaunch &L, double dt) {
+    if (L.p->n == 0) return cudaSuccess;
+    const StepArgs<T> a = make_step_args<T>(L);
+    const int64_t blocks = (L.p->n + 255) / 256;
+    const int grid = (int)(blocks < (int64_t)L.ctx->num_sms * 8 ? blocks : (int64_t)L.ctx->num_sms * 8);
+    if (L.f->kind == SFQ_FIELDS_PLANE_WAVE)
+        push_kernel<T, FK_PW><<<grid, 256, 0, L.stream>>>(a, (T)dt);
+    else
+        push_kernel<T, FK_SOA><<<grid, 256, 0, L.stream>>>(a, (T)dt);
     return cudaGetLastError();
 }
 

@@ -18,4 +18,5 @@ cudaError_t prepare_step_f32() {
 cudaError_t launch_fused_f32(const StepLaunch &L, uint32_t nsteps) {
     return L.ctx->inv_tr > 0 ? launch_fused_trunc_f32(L, nsteps) : launch_fused_t<float, false>(L, nsteps);
 }
+cudaError_t launch_push_f32(const StepLaunch &L, double dt) { return launch_push_t<float>(L, dt); }
 }  // namespace sfq

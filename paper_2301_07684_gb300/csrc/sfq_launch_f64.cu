@@ -18,4 +18,5 @@ cudaError_t prepare_step_f64() {
 cudaError_t launch_fused_f64(const StepLaunch &L, uint32_t nsteps) {
     return L.ctx->inv_tr > 0 ? launch_fused_trunc_f64(L, nsteps) : launch_fused_t<double, false>(L, nsteps);
 }
+cudaError_t launch_push_f64(const StepLaunch &L, double dt) { return launch_push_t<double>(L, dt); }
 }  // namespace sfq

@@ -231,13 +231,25 @@ __device__ __forceinline__ bool blcfa_phase_a(const StepArgs<T> &a, const T *s_n
     const T zeta = (T)2.220446049250313080847263336181640625e-16;
     const T zeta2 = (T)4.930380657631323783823303533017413935457540219431393779648e-32;
     const bool gate = (D > zeta2 * F2 * F2) && (chi > zeta);
+    const uint64_t id = a.id ? a.id[i] : a.id_base + (uint64_t)i;
+    const u4 w = draws(a.seed, id, a.step, (fl >> SFQ_TAG_SHIFT) & 3u);
+    const T r0 = uniform<T>(w.w[0]);
+    // Acceptance-rejection of the local method (Sec. 2): W~_rad(chi) <= W~_rad(0) = 5 pi / 2,
+    // so the same product with that bound (a margin above the fit's and Horner's rounding)
+    // majorises R dt.  Unless the majorant exceeds r (or 0.1, the threshold of the large-R dt
+    // counter), no event can occur and the fitted rate is not evaluated.
+    const T wmax = sizeof(T) == 4 ? (T)(7.8539816339744830962 * (1.0 + 1.52587890625e-05))
+                                  : (T)(7.8539816339744830962 * (1.0 + 9.094947017729282e-13));
+    const T dmax = a.prefdt * (chi * inv_g) * wmax;
+    if (!(dmax > r0) && !(dmax > (T)0.1)) {
+        c.v[C_OOR] += !(chi < pow2<T>(L<T>::NLC_EHI));                      // as the table would count it
+        return false;
+    }
     bool oor = false;
     const T d = a.prefdt * (chi * inv_g) * wtilde_rad<T>(s_nlc, chi, oor);
     c.v[C_OOR] += oor;
     c.v[C_RDT] += d > (T)0.1;
-    const uint64_t id = a.id ? a.id[i] : a.id_base + (uint64_t)i;
-    const u4 w = draws(a.seed, id, a.step, (fl >> SFQ_TAG_SHIFT) & 3u);
-    if (!(d > uniform<T>(w.w[0]))) return false;                            // local test
+    if (!(d > r0)) return false;                                            // local test
     ++c.v[C_EV];
     aux = (T)0;
     if (gate) {

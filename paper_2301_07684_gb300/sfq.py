@@ -93,6 +93,8 @@ def lib():
         L.sfq_mc_run_fused.argtypes = [vp, C.POINTER(Particles), C.POINTER(Fields), C.c_uint32, C.c_uint32,
                                        C.POINTER(Products), vp, vp]
         L.sfq_mc_run_fused.restype = st
+        L.sfq_push.argtypes = [vp, C.POINTER(Particles), C.POINTER(Fields), C.c_uint32, C.c_double, vp]
+        L.sfq_push.restype = st
         L.sfq_set_pair_rate_cutoff.argtypes = [vp, C.c_double]
         L.sfq_set_pair_rate_cutoff.restype = st
         L.sfq_set_sampler_coefficients.argtypes = [vp, C.c_int32]
@@ -141,7 +143,7 @@ def lib():
 
 EXPORTED = ["sfq_init", "sfq_finalize", "sfq_last_error", "sfq_constants", "sfq_photon_rate", "sfq_pair_rate",
             "sfq_uniforms", "sfq_sample_photon_xi", "sfq_sample_pair_xi", "sfq_mc_step", "sfq_mc_run",
-            "sfq_mc_run_fused", "sfq_set_pair_rate_cutoff", "sfq_set_sampler_coefficients",
+            "sfq_mc_run_fused", "sfq_push", "sfq_set_pair_rate_cutoff", "sfq_set_sampler_coefficients",
             "sfq_sampler_coefficients", "sfq_autotune_step", "sfq_sort_scratch_bytes", "sfq_sort_products", "sfq_sort_products_noalloc", "sfq_set_step_shape",
             "sfq_mlp_num_params", "sfq_mlp_create", "sfq_mlp_destroy", "sfq_mlp_get_params", "sfq_mlp_set_params",
             "sfq_mlp_loss_grad", "sfq_mlp_train", "sfq_mlp_predict_lnw", "sfq_mlp_plain_targets", "sfq_mlp_calibrate",
@@ -282,6 +284,11 @@ class Context:
         P, F, O = particles.descriptor(), fields.descriptor(), products.descriptor()
         self._check(lib().sfq_mc_run_fused(self._h, C.byref(P), C.byref(F), step0, nsteps, C.byref(O),
                                            _ptr(counters), _stream()), "sfq_mc_run_fused")
+
+    def push(self, particles: "ParticleBuffers", fields: "FieldSource", step: int, dt: float):
+        """One Boris push of the leptons' momenta in the fields at `step`."""
+        P, F = particles.descriptor(), fields.descriptor()
+        self._check(lib().sfq_push(self._h, C.byref(P), C.byref(F), step, float(dt), _stream()), "sfq_push")
 
     def set_pair_rate_cutoff(self, chi_min: float):
         """NBW rate zero below chi_min (0.01 by default; 0.3 gives the paper's "fast" rate)."""
