@@ -525,7 +525,13 @@ def run_ours(args):
             "clocks": main["clocks"],
             "fp64_path": None if f64 is None else {"value": f64["value"], "unit": UNIT, "ms_per_step": f64["ms_per_step"],
                           "achieved_gbs": f64["achieved_gbs"], "hbm_frac": f64["frac"],
-                          "steps": f64["steps"], "bound": "alu (fp64 pipe)"},
+                          "steps": f64["steps"], "bound": "alu (fp64 pipe)",
+                          "roofline": {"bound": "alu", "unit": "FP64 instructions/s",
+                                       "achieved": f64["value"] * args.fp64_inst_per_update,
+                                       "fp64_inst_per_update": args.fp64_inst_per_update,
+                                       "frac": args.fp64_pipe_busy,
+                                       "source": "ncu of the 2^22 capture: FP64-pipe instructions per update "
+                                                 "and sm__pipe_fp64_cycles_active (the pipe's busy fraction)"}},
             "plane_wave_fields": None if pw is None else {"value": pw["value"], "unit": UNIT, "ms_per_step": pw["ms_per_step"],
                                   "achieved_gbs": pw["achieved_gbs"], "frac": pw["frac"],
                                   "bytes_per_update": pw["bytes_per_update"]},
@@ -623,6 +629,10 @@ def main():
     # ncu capture summarised in profiles/mc_step_tma_fp32_soa_4M.md (4,194,304 particles;
     # the per-particle streams scale in proportion to n).  Re-measure whenever that kernel
     # changes, and pass --traffic-per-update 0 to report null meanwhile.
+    ap.add_argument("--fp64-inst-per-update", type=float, default=69.86,
+                    help="FP64-pipe instructions per update of the binary64 step kernel (ncu capture)")
+    ap.add_argument("--fp64-pipe-busy", type=float, default=0.874,
+                    help="sm__pipe_fp64_cycles_active of the binary64 step kernel (ncu capture)")
     ap.add_argument("--traffic-per-update", type=float, default=51.81,
                     help="DRAM bytes per update of the step kernel from an ncu capture (for roofline.traffic)")
     args = ap.parse_args()
