@@ -126,7 +126,12 @@ enum {
     SFQ_TAG_SHIFT = 4       /* bits 4-5: tag, the 4th word of the Philox counter */
 };
 enum { SFQ_ELECTRON = 0, SFQ_POSITRON = 1, SFQ_PHOTON = 2 };
-enum { SFQ_LEPTON_LCFA_OD = 0, SFQ_LEPTON_BLCFA_LOCAL = 1 };
+/* Lepton emission models: LCFA with the optical-depth method; beyond-LCFA (Sec. 5) by the
+ * local method with the Lorentz force E + beta x B at the particle; beyond-LCFA with the
+ * force taken from the pusher (Eqs. fl): the step first advances p^(n-1/2) by one Boris push
+ * (as sfq_push) to p^(n+1/2), which the particle keeps, and uses
+ * F_L = (p^(n+1/2) - p^(n-1/2)) / dt at p_L = (p^(n+1/2) + p^(n-1/2)) / 2. */
+enum { SFQ_LEPTON_LCFA_OD = 0, SFQ_LEPTON_BLCFA_LOCAL = 1, SFQ_LEPTON_BLCFA_PUSHED = 2 };
 
 /* Structure-of-arrays particle population (all device pointers). */
 typedef struct {
@@ -138,7 +143,7 @@ typedef struct {
     uint8_t *flags;           /* uint8[n] (in/out) */
     void *fprev[3];           /* real[n] each: BLCFA F_perp^(n-1) (in/out), NULL if unused */
     void *dfprev[3];          /* real[n] each: BLCFA F_perp^(n-1) - F_perp^(n-2) (in/out) */
-    int32_t lepton_model;     /* SFQ_LEPTON_LCFA_OD or SFQ_LEPTON_BLCFA_LOCAL */
+    int32_t lepton_model;     /* SFQ_LEPTON_LCFA_OD, SFQ_LEPTON_BLCFA_LOCAL or SFQ_LEPTON_BLCFA_PUSHED */
     int32_t reserved;
     const unsigned long long *n_dev;  /* optional device count: the step covers min(*n_dev, n)
                                          particles (a population grown on the device, e.g. the

@@ -167,6 +167,21 @@ def blcfa_update(p, E, B, dt, rho, Fprev, dF, just_created):
     return g, ev, list(fa), list(da), bool(jc.value)
 
 
+def blcfa_update_pushed(p, pn, dt, rho, Fprev, dF, just_created):
+    """One beyond-LCFA state update with the force from the pusher (Eqs. fl): p = p^(n-1/2),
+    pn = its push p_L^(n+1/2).  Returns (gate, eval, Fprev', dF', just_created')."""
+    L = lib()
+    f = L.orc_blcfa_update_pushed
+    f.restype = C.c_int
+    f.argtypes = [_PD, _PD, _D, _D, _PD, _PD, C.POINTER(C.c_uint8), C.POINTER(BlcfaEval)]
+    pa, na = (C.c_double * 3)(*p), (C.c_double * 3)(*pn)
+    fa, da = (C.c_double * 3)(*Fprev), (C.c_double * 3)(*dF)
+    jc = C.c_uint8(1 if just_created else 0)
+    ev = BlcfaEval()
+    g = f(pa, na, dt, rho, fa, da, C.byref(jc), C.byref(ev))
+    return g, ev, list(fa), list(da), bool(jc.value)
+
+
 def blcfa_threshold(F, delta, gamma, chi_):
     Fa = (C.c_double * 3)(*F)
     return lib().orc_blcfa_threshold(Fa, delta, gamma, chi_)
@@ -308,7 +323,7 @@ def uniforms_from_words(words):
 # --- Monte Carlo ------------------------------------------------------------
 SP_ELECTRON, SP_POSITRON, SP_PHOTON = 0, 1, 2
 FL_ALIVE, FL_JUST_CREATED = 1, 2
-MODE_LCFA_OD, MODE_BLCFA_LOCAL = 0, 1
+MODE_LCFA_OD, MODE_BLCFA_LOCAL, MODE_BLCFA_PUSHED = 0, 1, 2
 
 
 def mc_run(p, tau, ids, flags, species, fields, *, rho, dt, seed, step0=0, nsteps,

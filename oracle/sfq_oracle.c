@@ -443,23 +443,18 @@ typedef struct {
     int gate;          /* the two conditions below Eq. condit */
 } blcfa_eval;
 
-/* One update of the per-particle state (Eqs. fl ... condit).
- * READING (no pusher is in scope): the Lorentz force is the normalised
- * F_L = E + beta x B at the particle, p_L = p, gamma = sqrt(1 + p^2).
- * READING (first step after creation): F^(n-2) = F^(n-1) = F^(n) as stated
- * in Sec. 5, i.e. the stored difference becomes zero; the call signals no
- * emission at this step.  Returns the gate (0 for a just-created particle). */
-int orc_blcfa_update(const double p[3], const double E[3], const double B[3], double dt, double rho,
-                     double Fprev[3], double dF[3], uint8_t *just_created, blcfa_eval *out) {
+/* The common part of one update of the per-particle state (Eqs. fl_perp ... condit): pL is
+ * the momentum at the step, FL the Lorentz force on it.
+ * READING (first step after creation): F^(n-2) = F^(n-1) = F^(n) as stated in Sec. 5, i.e.
+ * the stored difference becomes zero; the call signals no emission at this step.  Returns
+ * the gate (0 for a just-created particle). */
+static int blcfa_core(const double pL[3], const double FL[3], double dt, double rho, double Fprev[3],
+                      double dF[3], uint8_t *just_created, blcfa_eval *out) {
     const double tauC = 1.0 / rho;
-    const double gamma = sqrt(1.0 + p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
-    const double b[3] = {p[0] / gamma, p[1] / gamma, p[2] / gamma};
-    const double FL[3] = {E[0] + b[1] * B[2] - b[2] * B[1],
-                          E[1] + b[2] * B[0] - b[0] * B[2],
-                          E[2] + b[0] * B[1] - b[1] * B[0]};
-    const double fp = (FL[0] * p[0] + FL[1] * p[1] + FL[2] * p[2]) / (gamma * gamma);
+    const double gamma = sqrt(1.0 + pL[0] * pL[0] + pL[1] * pL[1] + pL[2] * pL[2]);   /* Eq. gammaBLCFA */
+    const double fp = (FL[0] * pL[0] + FL[1] * pL[1] + FL[2] * pL[2]) / (gamma * gamma);
     double F[3];
-    for (int k = 0; k < 3; ++k) F[k] = FL[k] - fp * p[k];                 /* Eq. fl_perp */
+    for (int k = 0; k < 3; ++k) F[k] = FL[k] - fp * pL[k];               /* Eq. fl_perp */
     const double F2 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
     out->gamma = gamma;
     out->chi = tauC * gamma * sqrt(F2);                                    /* Eq. chi_p */
@@ -485,6 +480,30 @@ int orc_blcfa_update(const double p[3], const double E[3], const double B[3], do
     out->gate = (gamma * gamma * delta / (ORC_ZETA * ORC_ZETA) > out->chi * out->chi * F2) &&
                 (out->chi > ORC_ZETA);
     return out->gate;
+}
+
+/* One update without a pusher.  READING: the Lorentz force is the normalised
+ * F_L = E + beta x B at the particle and p_L = p. */
+int orc_blcfa_update(const double p[3], const double E[3], const double B[3], double dt, double rho,
+                     double Fprev[3], double dF[3], uint8_t *just_created, blcfa_eval *out) {
+    const double gamma = sqrt(1.0 + p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+    const double b[3] = {p[0] / gamma, p[1] / gamma, p[2] / gamma};
+    const double FL[3] = {E[0] + b[1] * B[2] - b[2] * B[1],
+                          E[1] + b[2] * B[0] - b[0] * B[2],
+                          E[2] + b[0] * B[1] - b[1] * B[0]};
+    return blcfa_core(p, FL, dt, rho, Fprev, dF, just_created, out);
+}
+
+/* One update with the force from the pusher (Eqs. fl): p is p^(n-1/2), pn = p_L^(n+1/2) its
+ * push over dt; F_L = (pn - p) / dt and p_L = (pn + p) / 2. */
+int orc_blcfa_update_pushed(const double p[3], const double pn[3], double dt, double rho, double Fprev[3],
+                            double dF[3], uint8_t *just_created, blcfa_eval *out) {
+    double FL[3], pL[3];
+    for (int k = 0; k < 3; ++k) {
+        FL[k] = (pn[k] - p[k]) / dt;
+        pL[k] = 0.5 * (pn[k] + p[k]);
+    }
+    return blcfa_core(pL, FL, dt, rho, Fprev, dF, just_created, out);
 }
 
 /* gamma_{gamma,LCFA}, Eq. gammaLCFA, with tau/tau_C = 2 pi sqrt(F^2/delta). */
@@ -632,14 +651,14 @@ int orc_num_threads(void) {
 /* ------------------------------------------------------------------------- */
 enum { SP_ELECTRON = 0, SP_POSITRON = 1, SP_PHOTON = 2 };
 enum { FL_ALIVE = 1, FL_JUST_CREATED = 2 };
-enum { MODE_LCFA_OD = 0, MODE_BLCFA_LOCAL = 1 };
+enum { MODE_LCFA_OD = 0, MODE_BLCFA_LOCAL = 1, MODE_BLCFA_PUSHED = 2 };
 
 /* Run parameters shared by all lineages. */
 typedef struct {
     double rho, pref, dt;
     uint64_t seed;
     uint32_t step0, nsteps;
-    int32_t lepton_mode;        /* MODE_LCFA_OD or MODE_BLCFA_LOCAL */
+    int32_t lepton_mode;        /* MODE_LCFA_OD, MODE_BLCFA_LOCAL or MODE_BLCFA_PUSHED */
     int32_t step_children;      /* 1: created leptons are stepped (beyond-LCFA chain) */
     double near_od;             /* |tau_d| <= near_od * tau0: optical-depth decision near threshold */
     double near_local;          /* |R dt - r| <= near_local * r: local decision near threshold */
@@ -789,7 +808,16 @@ static void step_lepton_blcfa(orc_state *s, const double E[3], const double B[3]
     blcfa_eval ev;
     const int was_new = (s->flags & FL_JUST_CREATED) != 0;
     uint8_t jc = (uint8_t)was_new;
-    const int gate = orc_blcfa_update(s->p, E, B, P->dt, P->rho, s->Fprev, s->dF, &jc, &ev);
+    int gate;
+    if (P->lepton_mode == MODE_BLCFA_PUSHED) {
+        /* the pusher advances p^(n-1/2) to p^(n+1/2) first; the particle keeps it */
+        double pn[3] = {s->p[0], s->p[1], s->p[2]};
+        orc_boris_push(pn, E, B, s->species == SP_ELECTRON ? -1.0 : 1.0, P->dt);
+        gate = orc_blcfa_update_pushed(s->p, pn, P->dt, P->rho, s->Fprev, s->dF, &jc, &ev);
+        for (int k = 0; k < 3; ++k) s->p[k] = pn[k];
+    } else {
+        gate = orc_blcfa_update(s->p, E, B, P->dt, P->rho, s->Fprev, s->dF, &jc, &ev);
+    }
     s->flags = (uint8_t)((s->flags & ~FL_JUST_CREATED) | (jc ? FL_JUST_CREATED : 0));
     if (was_new) return;                                        /* no emission after creation */
     double u[4];
@@ -823,7 +851,7 @@ static void step_particle(orc_state *s, const double *EB, uint32_t n, const orc_
     if (!(s->flags & FL_ALIVE)) return;
     const double *E = EB, *B = EB + 3;
     if (s->species == SP_PHOTON) step_photon(s, E, B, n, P, sink, info, children, nc);
-    else if (P->lepton_mode == MODE_BLCFA_LOCAL) step_lepton_blcfa(s, E, B, n, P, sink, info);
+    else if (P->lepton_mode != MODE_LCFA_OD) step_lepton_blcfa(s, E, B, n, P, sink, info);
     else step_lepton_od(s, E, B, n, P, sink, info);
 }
 

@@ -63,10 +63,11 @@ sfq_status validate_step(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields 
                          const sfq_spawn *spawn, const sfq_counters *counters) {
     if (!p || !f || !out) return fail(ctx, SFQ_ERR_ARG, "null descriptor");
     if (p->n < 0 || out->capacity < 0) return fail(ctx, SFQ_ERR_ARG, "negative size");
-    if (p->lepton_model != SFQ_LEPTON_LCFA_OD && p->lepton_model != SFQ_LEPTON_BLCFA_LOCAL)
+    if (p->lepton_model != SFQ_LEPTON_LCFA_OD && p->lepton_model != SFQ_LEPTON_BLCFA_LOCAL &&
+        p->lepton_model != SFQ_LEPTON_BLCFA_PUSHED)
         return fail(ctx, SFQ_ERR_ARG, "unknown lepton model");
     if (p->n == 0) return SFQ_OK;
-    if (p->lepton_model == SFQ_LEPTON_BLCFA_LOCAL) {
+    if (p->lepton_model != SFQ_LEPTON_LCFA_OD) {
         for (int k = 0; k < 3; ++k)
             if (!p->fprev[k] || !p->dfprev[k] || !aligned16(p->fprev[k]) || !aligned16(p->dfprev[k]))
                 return fail(ctx, SFQ_ERR_ARG, "beyond-LCFA state arrays null or misaligned");

@@ -150,6 +150,7 @@ static StepArgs<T> make_step_args(const StepLaunch &L) {
     a.inv_rho = (T)(1.0 / ctx->rho);
     a.rho = (T)ctx->rho;
     a.inv_dt = (T)(1.0 / ctx->cfg.dt);
+    a.dt = (T)ctx->cfg.dt;
     a.inv_dt2 = (T)(1.0 / (ctx->cfg.dt * ctx->cfg.dt));
     a.pair_chi_min = (T)ctx->pair_chi_min;
     a.tab = tables_of<T>(ctx);
@@ -170,7 +171,7 @@ static cudaError_t launch_step_t(const StepLaunch &L) {
     const int cw = TRUNC ? TRUNC_CW : ((L.ppt == 8 || L.ppt == 16 || L.ppt == 20) ? L.ppt : 16);
     const int tile = cw * (sizeof(T) == 4 ? 64 : 32);
     // the beyond-LCFA model runs on the warp-streaming kernel (its state is read directly)
-    const bool tma = p.lepton_model != SFQ_LEPTON_BLCFA_LOCAL &&
+    const bool tma = p.lepton_model == SFQ_LEPTON_LCFA_OD &&
                      (L.variant == 2 || (L.variant == 0 && p.n >= (int64_t)tile * ctx->num_sms));
     if (tma) {
         void (*kern)(const StepArgs<T>) = nullptr;

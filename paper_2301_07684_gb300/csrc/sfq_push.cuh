@@ -11,28 +11,6 @@
 
 namespace sfq {
 
-template <typename T>
-__device__ __forceinline__ void boris(T u[3], const T E[3], const T B[3], T q, T dt) {
-    const T h = (T)0.5 * q * dt;
-    T um[3], t[3], s[3], up[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) um[k] = fma(h, E[k], u[k]);
-    const T gm = sqrt(fma(um[0], um[0], fma(um[1], um[1], fma(um[2], um[2], (T)1))));
-    const T hg = h / gm;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) t[k] = hg * B[k];
-    const T f = (T)2 / fma(t[0], t[0], fma(t[1], t[1], fma(t[2], t[2], (T)1)));
-#pragma unroll
-    for (int k = 0; k < 3; ++k) s[k] = f * t[k];
-    const T c0 = um[1] * t[2] - um[2] * t[1], c1 = um[2] * t[0] - um[0] * t[2], c2 = um[0] * t[1] - um[1] * t[0];
-    const T v0 = um[0] + c0, v1 = um[1] + c1, v2 = um[2] + c2;
-    up[0] = um[0] + (v1 * s[2] - v2 * s[1]);
-    up[1] = um[1] + (v2 * s[0] - v0 * s[2]);
-    up[2] = um[2] + (v0 * s[1] - v1 * s[0]);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) u[k] = fma(h, E[k], up[k]);
-}
-
 // One push of every alive lepton of the population at the launch's step (fields as the
 // step reads them); photons and dead particles are left as they are.
 template <typename T, int FK>

@@ -154,7 +154,7 @@ sfq_status sfq_autotune_step(sfq_ctx *ctx, const sfq_particles *p, const sfq_fie
     if (n <= 0) return fail(ctx, SFQ_ERR_ARG, "no particles to time");
     const bool fp64 = ctx->cfg.precision == SFQ_FP64;
     const size_t es = fp64 ? 8 : 4;
-    const bool blcfa = p->lepton_model == SFQ_LEPTON_BLCFA_LOCAL;
+    const bool blcfa = p->lepton_model != SFQ_LEPTON_LCFA_OD;
     const int64_t pcap = 2 * n + 1024;
     // one allocation: particle copy, pristine copy of the mutable state, products, counters
     auto a256 = [](size_t b) { return (b + 255) & ~(size_t)255; };

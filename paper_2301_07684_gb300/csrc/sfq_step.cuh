@@ -57,6 +57,7 @@ struct StepArgs {
     T inv_rho;       // 1 / rho
     T rho;
     T inv_dt, inv_dt2;
+    T dt;            // timestep (the pusher of the BLCFA_PUSHED model)
     T pair_chi_min;  // NBW rate is zero below this chi (0.01, or the "fast" cutoff)
     Tables<T> tab;
     sfq_counters *counters;
@@ -197,11 +198,28 @@ template <typename T>
 __device__ __forceinline__ bool blcfa_phase_a(const StepArgs<T> &a, const T *s_nlc, int64_t i, uint8_t fl, T px,
                                               T py, T pz, const T E[3], const T B[3], T &g, T &chi, T &aux,
                                               Cnt &c) {
+    T FL[3];
+    if (a.lepton_model == SFQ_LEPTON_BLCFA_PUSHED) {
+        // the pusher advances p^(n-1/2) to p_L^(n+1/2); F_L = (p_L^(n+1/2) - p^(n-1/2)) / dt and
+        // p_L^(n) = (p_L^(n+1/2) + p^(n-1/2)) / 2 (Eqs. fl); the particle keeps the pushed momentum
+        T u[3] = {px, py, pz};
+        const int sp = (fl >> SFQ_SPECIES_SHIFT) & 3;
+        boris<T>(u, E, B, sp == SFQ_ELECTRON ? (T)-1 : (T)1, a.dt);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) FL[k] = (u[k] - (k == 0 ? px : k == 1 ? py : pz)) * a.inv_dt;
+        a.px[i] = u[0]; a.py[i] = u[1]; a.pz[i] = u[2];
+        px = (T)0.5 * (u[0] + px); py = (T)0.5 * (u[1] + py); pz = (T)0.5 * (u[2] + pz);
+    }
     const T g2 = fma(px, px, fma(py, py, fma(pz, pz, (T)1)));
     const T inv_g = rsqrt_nr(g2);
     g = sqrt_nr(g2);
-    const T bx = px * inv_g, by = py * inv_g, bz = pz * inv_g;
-    const T FL[3] = {E[0] + (by * B[2] - bz * B[1]), E[1] + (bz * B[0] - bx * B[2]), E[2] + (bx * B[1] - by * B[0])};
+    if (a.lepton_model != SFQ_LEPTON_BLCFA_PUSHED) {
+        // without a pusher: F_L = E + beta x B at the particle, p_L = p (reading R9)
+        const T bx = px * inv_g, by = py * inv_g, bz = pz * inv_g;
+        FL[0] = E[0] + (by * B[2] - bz * B[1]);
+        FL[1] = E[1] + (bz * B[0] - bx * B[2]);
+        FL[2] = E[2] + (bx * B[1] - by * B[0]);
+    }
     const T fp = (FL[0] * px + FL[1] * py + FL[2] * pz) * inv_g * inv_g;
     const T F[3] = {FL[0] - fp * px, FL[1] - fp * py, FL[2] - fp * pz};      // Eq. fl_perp
     const T F2 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
@@ -543,7 +561,7 @@ __global__ void __launch_bounds__(STEP_BS, SFQ_STEP_MINB) mc_step_kernel(const S
             if (i < n_eff) {
                 const uint8_t fl = a.flags[i];
                 const bool photon_f = ((fl >> SFQ_SPECIES_SHIFT) & 3) == SFQ_PHOTON;
-                if ((fl & SFQ_ALIVE) && !photon_f && a.lepton_model == SFQ_LEPTON_BLCFA_LOCAL) {
+                if ((fl & SFQ_ALIVE) && !photon_f && a.lepton_model != SFQ_LEPTON_LCFA_OD) {
                     T E[3], B[3];
                     load_fields<T, FK>(a, i, E, B);
                     ev = blcfa_phase_a<T>(a, s_nlc, i, fl, a.px[i], a.py[i], a.pz[i], E, B, g, chi, aux, c);

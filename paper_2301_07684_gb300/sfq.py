@@ -21,7 +21,7 @@ SFQ_FP32, SFQ_FP64 = 0, 1
 SFQ_ALIVE, SFQ_JUST_CREATED = 1, 2
 SFQ_SPECIES_SHIFT, SFQ_TAG_SHIFT = 2, 4
 SFQ_ELECTRON, SFQ_POSITRON, SFQ_PHOTON = 0, 1, 2
-SFQ_LEPTON_LCFA_OD, SFQ_LEPTON_BLCFA_LOCAL = 0, 1
+SFQ_LEPTON_LCFA_OD, SFQ_LEPTON_BLCFA_LOCAL, SFQ_LEPTON_BLCFA_PUSHED = 0, 1, 2
 SFQ_FIELDS_SOA, SFQ_FIELDS_PLANE_WAVE = 0, 1
 STATUS = {0: "SFQ_OK", 1: "SFQ_ERR_ARG", 2: "SFQ_ERR_CUDA", 3: "SFQ_ERR_CAPACITY", 4: "SFQ_ERR_TABLE",
           5: "SFQ_ERR_RANGE", 6: "SFQ_ERR_TIMEOUT"}

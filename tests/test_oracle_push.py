@@ -67,3 +67,21 @@ def test_photons_unchanged(O):
     u = np.array([[1.0, 2.0, 3.0]])
     un = O.boris_push(u.copy(), [[1.0, 1.0, 1.0]], [[2.0, 0.0, 1.0]], [0.0], 0.1)
     np.testing.assert_array_equal(un, u)
+
+
+def test_pushed_force_in_a_magnetic_field(O):
+    """With the pusher, F_L = (p^(n+1/2) - p^(n-1/2)) / dt (Eqs. fl).  In a magnetic field
+    alone the Boris push is the implicit midpoint rule, so F_L = q p_L x B / gamma(p) with
+    p_L the mid-point momentum, exactly; it is perpendicular to p_L, so F_perp = F_L, and
+    chi_p = tau_C gamma(p_L) |F_perp|."""
+    g = np.random.default_rng(7)
+    rho, dt = 3.2972e5, 0.0628
+    for _ in range(32):
+        p = g.normal(0.0, 300.0, 3)
+        B = g.normal(0.0, 80.0, 3)
+        pn = O.boris_push(p.copy(), np.zeros(3), B, -1.0, dt)[0]
+        _, ev, _, _, _ = O.blcfa_update_pushed(p, pn, dt, rho, [0.0] * 3, [0.0] * 3, True)
+        pL = 0.5 * (p + pn)
+        F = -np.cross(pL, B) / np.sqrt(1.0 + p @ p)
+        np.testing.assert_allclose(np.array(ev.F[:]), F, rtol=1e-9, atol=1e-12 * np.abs(F).max())
+        assert ev.chi == pytest.approx(np.sqrt(1.0 + pL @ pL) * np.linalg.norm(F) / rho, rel=1e-12)
