@@ -2,8 +2,8 @@
 //
 // Philox4x32-10 (Salmon et al., SC'11), the uniform map of the step, exact piece
 // selection for the fitted tables (binary exponent + top mantissa bits), Horner
-// evaluation, and the binary64 optical depth updated in fixed point on the
-// integer pipe.
+// evaluation, and the exact widening of a binary32 decrement for the binary64 optical
+// depth.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -220,58 +220,6 @@ __device__ __forceinline__ float rsqrt_nr(float q) {
 __device__ __forceinline__ double rsqrt_nr(double q) { return rsqrt(q); }
 
 // ---------------------------------------------------------------------------
-// Optical depth in binary64 updated on the integer pipe (GB300's FP64 pipe runs at
-// about 1/70 of the FP32 rate).  tau in [0, 32) maps exactly onto 2^-58 fixed point
-// when tau >= 2^-6 (finer values are truncated below 2^-58); the binary32 decrement
-// d maps exactly when d >= 2^-35.  The difference is rounded once to binary64
-// (round to nearest even), as a binary64 subtraction would do.
-constexpr int TAU_FIX = 58;
-
-// Returns false when tau is outside [0, 32) (caller takes the binary64 path).
-__device__ __forceinline__ bool tau_to_fixed(uint64_t b, uint64_t &q) {
-    if (b >> 63) return false;                       // negative (or -0)
-    const int e = (int)(b >> 52);                    // biased exponent
-    if (e == 0) { q = 0ull; return true; }           // +0 or subnormal
-    const int sh = e - 1075 + TAU_FIX;               // value = m 2^(e-1075)
-    if (sh > 10) return false;                       // tau >= 32, Inf or NaN
-    const uint64_t m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    q = sh >= 0 ? (m << sh) : (sh <= -64 ? 0ull : (m >> (-sh)));
-    return true;
-}
-
-// binary32 d >= 0 -> floor(d 2^58) as an unsigned value; d >= 32 (also Inf/NaN)
-// returns UINT64_MAX, larger than any tau in [0, 32).
-__device__ __forceinline__ uint64_t dec_to_fixed(float d) {
-    const uint32_t b = __float_as_uint(d);
-    const int e = (int)(b >> 23);
-    if (e == 0 || (b >> 31)) return 0ull;
-    const int sh = e - 150 + TAU_FIX;                // value = m 2^(e-150)
-    if (sh > 39) return ~0ull;                       // d >= 32
-    const uint64_t m = (b & 0x7FFFFFu) | 0x800000u;
-    return sh >= 0 ? (m << sh) : (sh <= -64 ? 0ull : (m >> (-sh)));
-}
-
-// fixed point (< 2^63) -> binary64 bits, round to nearest even.
-__device__ __forceinline__ uint64_t fixed_to_tau(uint64_t u) {
-    if (u == 0) return 0ull;
-    const int msb = 63 - __clzll((long long)u);
-    uint64_t m;
-    int ex = msb;
-    if (msb > 52) {
-        const int sh = msb - 52;
-        m = u >> sh;
-        const uint64_t rem = u & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-        if (rem > half || (rem == half && (m & 1ull))) {
-            ++m;
-            if (m >> 53) { m >>= 1; ++ex; }
-        }
-    } else {
-        m = u << (52 - msb);
-    }
-    const uint64_t be = (uint64_t)(ex - TAU_FIX + 1023);
-    return (be << 52) | (m & 0xFFFFFFFFFFFFFull);
-}
-
 // binary32 -> binary64 bits for a finite positive normal value (exact), on 32-bit halves:
 // the high word is the binary32 pattern shifted right by 3 with the exponent rebiased by
 // 1023 - 127 = 896; the low word holds the last 3 mantissa bits.
