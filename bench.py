@@ -483,7 +483,39 @@ def run_ours(args):
         torch.cuda.empty_cache()
         return res
 
+    def config1_leg():
+        """Config 1 (FP64, no time stepping): latency of the rate and sampling entry points on
+        4096 electrons and 4096 photons, one Philox draw each."""
+        d1 = W.config1()
+        ctx = sfq.Context(ref_len_m=W.REF_LEN, dt=W.DT, precision="fp64", seed=0, device=local)
+        T = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(device=device, dtype=torch.float64)
+        ge, xe, gg, xg = T(d1["gamma_e"]), T(d1["chi_e"]), T(d1["gamma_g"]), T(d1["chi_g"])
+        ids = torch.as_tensor(d1["id_e"].astype(np.int64)).to(device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+        def calls():
+            r = ctx.uniforms(ids, step=0, tag=0)[:, 1].contiguous()
+            ctx.photon_rate(ge, xe)
+            ctx.pair_rate(gg, xg)
+            ctx.sample_photon_xi(xe, r)
+            ctx.sample_pair_xi(xg, r)
+
+        for _ in range(3):
+            calls()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(10):
+            e0.record()
+            calls()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ctx.close()
+        return {"workload": "config 1: 4096 e- and 4096 photons, both rates and one energy sample each, FP64",
+                "ms": statistics.median(ts), "calls": 5}
+
     legs = set(args.legs.split(","))
+    config1 = config1_leg() if "config1" in legs else None
     main = one_path("fp32", "soa", args.steps, args.warmup, with_e2e=True)
     fused = fused_leg("fp32") if "fused" in legs and args.fused else None
     fused64 = fused_leg("fp64") if "fused64" in legs and args.fused else None
@@ -539,6 +571,7 @@ def run_ours(args):
                 "value": trunc["value"], "unit": UNIT, "ms_per_step": trunc["ms_per_step"], "frac": trunc["frac"],
                 "note": "headline workload with the inverse-CDF pieces cut to 8 x 8 Chebyshev coefficients "
                         "(sfq_set_sampler_coefficients; worst w-bar error 6.3e-7)"},
+            "config1_latency": config1,
             "fused_plane_wave": fused,
             "fused_plane_wave_fp64": fused64,
             "batched": batched,
@@ -573,11 +606,34 @@ def oracle_sample_run(n_sample, nsteps, step0=0):
     return n_sample * nsteps, dt, O.num_threads()
 
 
+def oracle_config1(n_sample=1024):
+    """The oracle on config 1: the first n_sample of its 4096 electrons and 4096 photons, both
+    rates and one energy sample each (quadrature and Brent roots).  Returns the seconds it
+    took and the time scaled to the full config."""
+    from oracle import oracle as O
+    from paper_2301_07684_gb300 import workloads as W
+    O.build()
+    d = W.config1()
+    k = slice(0, n_sample)
+    r = O.uniforms_from_words(O.philox(d["id_e"][k], 0, 0, 0))[:, 1]
+    pref = O.rate_prefactor(W.RHO)
+    t = time.perf_counter()
+    O.photon_rate(d["gamma_e"][k], d["chi_e"][k], pref)
+    O.pair_rate(d["gamma_g"][k], d["chi_g"][k], pref)
+    O.photon_s(r, d["chi_e"][k])
+    O.pair_shares(r, d["chi_g"][k])
+    sec = time.perf_counter() - t
+    return {"sample": f"{n_sample} electrons and {n_sample} photons of config 1", "s": sec,
+            "full_config_s": sec * d["chi_e"].size / n_sample}
+
+
 def cpu_baseline(args):
     upd, sec, thr = oracle_sample_run(args.oracle_particles, args.oracle_steps)
+    c1 = oracle_config1() if args.oracle_config1 else None
     return {"value": upd / sec, "unit": UNIT, "cores": thr, "kind": "oracle",
             "sample": f"{args.oracle_particles} particles x {args.oracle_steps} steps of the same workload "
-                      f"({upd} updates in {sec:.1f} s)"}
+                      f"({upd} updates in {sec:.1f} s)",
+            "config1": c1}
 
 
 def run_reference(args):
@@ -619,10 +675,11 @@ def main():
     ap.add_argument("--surrogate-steps", type=int, default=30000,
                     help="training steps of the surrogate leg (0 skips it)")
     ap.add_argument("--fused", type=int, default=1, help="time the fused multi-step plane-wave run (0: skip)")
-    ap.add_argument("--legs", default="pw,fp64,trunc,fused,fused64,batched,surrogate",
+    ap.add_argument("--legs", default="config1,pw,fp64,trunc,fused,fused64,batched,surrogate",
                     help="legs timed beside the headline step (comma list; the headline always runs)")
     ap.add_argument("--shape", default="",
                     help="fixed launch shape 'variant:shape' of the per-step legs (e.g. 2:16) instead of the autotuner")
+    ap.add_argument("--oracle-config1", type=int, default=1, help="also time the oracle on config 1 (0: skip)")
     ap.add_argument("--oracle-particles", type=int, default=512)
     ap.add_argument("--oracle-steps", type=int, default=50)
     # DRAM bytes (read + write) per update of mc_step_tma_kernel<float, SoA, 16 warps>, from the
