@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(FUSED_BS, 2) mc_fused_kernel(const StepArgs<T>
     using RS = RateSmem<T>;
     __shared__ __align__(16) T s_nlc[RS::NLC_N];
     __shared__ __align__(16) T s_nbw[RS::NBW_N];
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     FEntry<T> *q = reinterpret_cast<FEntry<T> *>(smem) + (size_t)warp * QS;
     EvOut<T> *res = reinterpret_cast<EvOut<T> *>(smem + CFG::O_RES) + (size_t)warp * QS;

@@ -137,19 +137,22 @@ __device__ __forceinline__ T chi_pw(T g, T px, T py, T f, T inv_rho) {
     return sqrt_nr(q) * inv_rho;
 }
 
-// Optical-depth decrement (Sec. 2).  Returns true on an event; otherwise stores
-// the new tau.  `draw0` holds -ln(u3) when the particle arrived without one.
+// Optical-depth decrement (Sec. 2).  od_update returns true on an event; otherwise it
+// stores the new tau.  It is od_fill followed by od_sub.
+// The optical depth a particle starts from: its stored bits, or a fresh draw -ln(u3) when
+// it arrived without one (sign bit set).
 template <typename IdF>
-__device__ __forceinline__ bool od_update(double *tau_ptr, float d, uint64_t seed, IdF id_of,
-                                          uint32_t step, uint32_t tag) {
-    uint64_t b = (uint64_t)__double_as_longlong(*tau_ptr);
+__device__ __forceinline__ uint64_t od_fill(uint64_t b, uint64_t seed, IdF id_of, uint32_t step, uint32_t tag) {
     if (b >> 63) {                                  // no optical depth yet: draw it (word 3)
         const u4 w = draws(seed, id_of(), step, tag);
         const float t0 = -logf(uniform<float>(w.w[3]));
         b = f32_to_f64_bits(t0);
     }
-    // tau_d - R dt in binary64: the binary32 decrement is widened exactly with integer
-    // operations and the subtraction is the only binary64 instruction of the update
+    return b;
+}
+// tau_d - R dt in binary64: the binary32 decrement is widened exactly with integer
+// operations and the subtraction is the only binary64 instruction of the update
+__device__ __forceinline__ bool od_sub(double *tau_ptr, uint64_t b, float d) {
     const uint32_t db = __float_as_uint(d);
     const uint64_t dd = ((db >> 23) - 1u < 254u) ? f32_to_f64_bits(d) : 0ull;   // normal d > 0, else 0
     const double t = __dsub_rn(__longlong_as_double((long long)b), __longlong_as_double((long long)dd));
@@ -158,6 +161,12 @@ __device__ __forceinline__ bool od_update(double *tau_ptr, float d, uint64_t see
     if (__double_as_longlong(t) < 0) return true;
     *tau_ptr = t;
     return false;
+}
+template <typename IdF>
+__device__ __forceinline__ bool od_update(double *tau_ptr, float d, uint64_t seed, IdF id_of,
+                                          uint32_t step, uint32_t tag) {
+    const uint64_t b = od_fill((uint64_t)__double_as_longlong(*tau_ptr), seed, id_of, step, tag);
+    return od_sub(tau_ptr, b, d);
 }
 template <typename IdF>
 __device__ __forceinline__ bool od_update(double *tau_ptr, double d, uint64_t seed, IdF id_of,
@@ -520,6 +529,43 @@ __device__ __forceinline__ bool step_particle_v(const StepArgs<T> &a, const T *s
     c.v[C_RDT] += d > (T)0.1;
     const auto id_of = [&]() { return a.id ? a.id[i] : a.id_base + (uint64_t)i; };
     return od_update(&tau, d, a.seed, id_of, step, (fl >> SFQ_TAG_SHIFT) & 3u);
+}
+
+// Two alive leptons of one lane, binary32: the arithmetic of step_particle_v for each,
+// written as one block with the rare optical-depth draw in front, so that nothing
+// branches between the two dependency chains and they interleave.  The NaN guard of
+// step_particle_v becomes a select (the rate is evaluated at chi = 0 and discarded).
+template <bool PW>
+__device__ __forceinline__ void step_lepton_pair(const StepArgs<float> &a, const float *s_nlc, int64_t i0,
+                                                 const uint8_t fl[2], const float px[2], const float py[2],
+                                                 const float pz[2], const float E[2][3], const float B[2][3],
+                                                 double tau[2], float g[2], float chi[2], bool ev[2], Cnt &c) {
+    uint64_t b[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const auto id_of = [&]() { return a.id ? a.id[i0 + k] : a.id_base + (uint64_t)(i0 + k); };
+        b[k] = od_fill((uint64_t)__double_as_longlong(tau[k]), a.seed, id_of, a.step, (fl[k] >> SFQ_TAG_SHIFT) & 3u);
+    }
+    float d[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float p2 = fmaf(px[k], px[k], fmaf(py[k], py[k], pz[k] * pz[k]));
+        const float g2 = 1.0f + p2;
+        const float inv_g = g2 > 0.0f ? rsqrt_nr(g2) : 0.0f;
+        g[k] = g2 * inv_g;
+        chi[k] = PW ? chi_pw<float>(g[k], px[k], py[k], E[k][1], a.inv_rho)
+                    : chi_of<float>(g[k], px[k], py[k], pz[k], E[k], B[k], a.inv_rho);
+        const bool ok = chi[k] >= 0.0f && g[k] > 0.0f;
+        bool oor = false;
+        const float w = wtilde_rad<float>(s_nlc, ok ? chi[k] : 0.0f, oor);
+        d[k] = ok ? a.prefdt * (chi[k] * inv_g) * w : 0.0f;
+        c.v[C_UPD] += 1;
+        c.v[C_NAN] += !ok;
+        c.v[C_OOR] += ok && oor;
+        c.v[C_RDT] += d[k] > 0.1f;
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) ev[k] = od_sub(&tau[k], b[k], d[k]);
 }
 
 // T: float (mixed) or double; FK: field source; PPT: particles per lane per chunk.

@@ -225,36 +225,61 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
                 }
             }
             double tau_out[2] = {vt.x, vt.y};
+            // the fields of particle li0 + k
+            const auto fields = [&](int k, T E[3], T B[3]) {
+                if (FK == FK_SOA) {
+#pragma unroll
+                    for (int c3 = 0; c3 < 3; ++c3) {
+                        E[c3] = k == 0 ? vE[c3].x : vE[c3].y;
+                        B[c3] = k == 0 ? vB[c3].x : vB[c3].y;
+                    }
+                } else {
+                    uint32_t kk = reinterpret_cast<const uint32_t *>(st + S::O_K0)[li0 + k] + a.pw_offset;
+                    kk -= (kk >= a.n_table) ? a.n_table : 0u;
+                    kk = kk < a.n_table ? kk : a.n_table - 1u;
+                    const T amp = has_amp ? reinterpret_cast<const T *>(st + S::O_AMP)[li0 + k] : a.amp0;
+                    const T f = amp * __ldg(a.pw_table + kk);
+                    E[0] = (T)0; E[1] = f; E[2] = (T)0;
+                    B[0] = (T)0; B[1] = (T)0; B[2] = f;
+                }
+            };
+            const uint8_t fl2[2] = {(uint8_t)(vf & 0xFF), (uint8_t)(vf >> 8)};
+            const auto lepton = [](uint8_t fl) {
+                return (fl & SFQ_ALIVE) && ((fl >> SFQ_SPECIES_SHIFT) & 3) != SFQ_PHOTON;
+            };
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                const uint8_t fl = (uint8_t)(k == 0 ? (vf & 0xFF) : (vf >> 8));
-                ev[k] = false;
-                gk[k] = (T)0;
-                ck[k] = (T)0;
                 pk[k][0] = k == 0 ? vx.x : vx.y;
                 pk[k][1] = k == 0 ? vy.x : vy.y;
                 pk[k][2] = k == 0 ? vz.x : vz.y;
-                fk[k] = fl;
-                if (fl & SFQ_ALIVE) {
-                    T E[3], B[3];
-                    if (FK == FK_SOA) {
+                fk[k] = fl2[k];
+            }
+            bool done = false;
+            if constexpr (PAIRED) {
+                if (lepton(fl2[0]) && lepton(fl2[1])) {
+                    // the common case: two alive leptons, stepped as one straight-line block
+                    T E2[2][3], B2[2][3];
+                    fields(0, E2[0], B2[0]);
+                    fields(1, E2[1], B2[1]);
+                    const T px2[2] = {vx.x, vx.y}, py2[2] = {vy.x, vy.y}, pz2[2] = {vz.x, vz.y};
+                    step_lepton_pair<FK == FK_PW>(a, s_nlc, start + li0, fl2, px2, py2, pz2, E2, B2, tau_out, gk,
+                                                  ck, ev, c);
+                    done = true;
+                }
+            }
+            if (!done) {
 #pragma unroll
-                        for (int c3 = 0; c3 < 3; ++c3) {
-                            E[c3] = k == 0 ? vE[c3].x : vE[c3].y;
-                            B[c3] = k == 0 ? vB[c3].x : vB[c3].y;
-                        }
-                    } else {
-                        uint32_t kk = reinterpret_cast<const uint32_t *>(st + S::O_K0)[li0 + k] + a.pw_offset;
-                        kk -= (kk >= a.n_table) ? a.n_table : 0u;
-                        kk = kk < a.n_table ? kk : a.n_table - 1u;
-                        const T amp = has_amp ? reinterpret_cast<const T *>(st + S::O_AMP)[li0 + k] : a.amp0;
-                        const T f = amp * __ldg(a.pw_table + kk);
-                        E[0] = (T)0; E[1] = f; E[2] = (T)0;
-                        B[0] = (T)0; B[1] = (T)0; B[2] = f;
+                for (int k = 0; k < 2; ++k) {
+                    ev[k] = false;
+                    gk[k] = (T)0;
+                    ck[k] = (T)0;
+                    if (fl2[k] & SFQ_ALIVE) {
+                        T E[3], B[3];
+                        fields(k, E, B);
+                        ev[k] = step_particle_v<T, FK == FK_PW>(a, s_nlc, s_nbw, start + li0 + k, fl2[k], pk[k][0],
+                                                                pk[k][1], pk[k][2], E, B, tau_out[k], gk[k], ck[k],
+                                                                c, a.step);
                     }
-                    ev[k] = step_particle_v<T, FK == FK_PW>(a, s_nlc, s_nbw, start + li0 + k, fl, k == 0 ? vx.x : vx.y,
-                                               k == 0 ? vy.x : vy.y, k == 0 ? vz.x : vz.y, E, B, tau_out[k],
-                                               gk[k], ck[k], c, a.step);
                 }
             }
             // both optical depths in one 16-byte store (an event particle's value is
