@@ -37,11 +37,16 @@ class RunParams(C.Structure):
     _fields_ = [("rho", C.c_double), ("pref", C.c_double), ("dt", C.c_double),
                 ("seed", C.c_uint64), ("step0", C.c_uint32), ("nsteps", C.c_uint32),
                 ("lepton_mode", C.c_int32), ("step_children", C.c_int32),
-                ("near_od", C.c_double), ("near_local", C.c_double), ("near_blcfa", C.c_double)]
+                ("near_od", C.c_double), ("near_local", C.c_double), ("near_blcfa", C.c_double),
+                ("cascade", C.c_int32), ("reserved", C.c_int32)]
 
 
 PRODUCT_DTYPE = np.dtype([("p", "<f8", (3,)), ("parent_id", "<u8"), ("step", "<u4"),
                           ("parent_tag", "<u4"), ("species", "<u4"), ("member", "<u4")], align=True)
+
+CASCADE_DTYPE = np.dtype([("p", "<f8", (3,)), ("tau", "<f8"), ("id", "<u8"), ("parent_id", "<u8"),
+                          ("root", "<i8"), ("step", "<u4"), ("member", "<u4"), ("flags", "u1"),
+                          ("species", "u1"), ("pad", "u1", (6,))], align=True)
 
 _D = C.c_double
 _PD = C.POINTER(C.c_double)
@@ -372,3 +377,64 @@ def mc_run(p, tau, ids, flags, species, fields, *, rho, dt, seed, step0=0, nstep
         raise RuntimeError(f"oracle product capacity {cap_products} < {k}")
     return dict(p=p, tau=tau, flags=flags, fprev=fprev, dfprev=dfprev, products=prod[:k].copy(),
                 first_near_step=first_near, n_events=n_events)
+
+
+def child_id(seed, parent, parent_tag, step, member):
+    """Id of a particle created in a full cascade (orc_child_id): bit 63 set over the first
+    two Philox words of the counter (parent id, step, 0x100 | parent tag << 2 | member)."""
+    f = lib().orc_child_id
+    f.restype = C.c_uint64
+    f.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32]
+    return int(f(int(seed), int(parent), int(parent_tag), int(step), int(member)))
+
+
+def mc_cascade(p, tau, ids, flags, species, fields, *, rho, dt, seed, step0=0, nsteps,
+               fprev=None, dfprev=None, lepton_mode=MODE_LCFA_OD, near_od=1e-6, near_local=1e-6,
+               near_blcfa=1e-4, cap_products=None, cap_out=None):
+    """Full cascade of independent primaries (orc_mc_cascade): every product is also a
+    particle, stepped from the next step on in its primary's field.  ``fields`` has shape
+    (n, nsteps, 6).  Returns the primaries' final state, the product records, every created
+    particle (CASCADE_DTYPE) and per-primary lineage info."""
+    L = lib()
+    n = len(ids)
+    p = np.ascontiguousarray(np.array(p, dtype=np.float64).reshape(n, 3))
+    tau = np.ascontiguousarray(np.array(tau, dtype=np.float64).reshape(n))
+    ids = np.ascontiguousarray(np.asarray(ids, dtype=np.uint64))
+    flags = np.ascontiguousarray(np.array(flags, dtype=np.uint8))
+    species = np.ascontiguousarray(np.asarray(species, dtype=np.uint8))
+    fields = np.ascontiguousarray(np.asarray(fields, dtype=np.float64).reshape(n, nsteps, 6))
+    fp = dfp = None
+    if fprev is not None:
+        fprev = np.ascontiguousarray(np.array(fprev, dtype=np.float64).reshape(n, 3))
+        dfprev = np.ascontiguousarray(np.array(dfprev, dtype=np.float64).reshape(n, 3))
+        fp, dfp = _p(fprev), _p(dfprev)
+    for _ in range(2):
+        cp = cap_products if cap_products is not None else max(256, 16 * n * nsteps)
+        co = cap_out if cap_out is not None else max(256, 16 * n * nsteps)
+        prod = np.zeros(cp, dtype=PRODUCT_DTYPE)
+        out = np.zeros(co, dtype=CASCADE_DTYPE)
+        nprod, nout = C.c_int64(0), C.c_int64(0)
+        first_near = np.empty(n, dtype=np.int32)
+        n_events = np.empty(n, dtype=np.int32)
+        P = RunParams(rho=rho, pref=rate_prefactor(rho), dt=dt, seed=seed, step0=step0, nsteps=nsteps,
+                      lepton_mode=lepton_mode, step_children=1, near_od=near_od, near_local=near_local,
+                      near_blcfa=near_blcfa, cascade=1, reserved=0)
+        f = L.orc_mc_cascade
+        f.restype = C.c_int
+        f.argtypes = [_I64] + [C.c_void_p] * 8 + [C.POINTER(RunParams), C.c_void_p, _I64, C.POINTER(C.c_int64),
+                                                  C.c_void_p, _I64, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p]
+        p1, tau1, fl1 = p.copy(), tau.copy(), flags.copy()
+        fp1 = fprev.copy() if fprev is not None else None
+        dfp1 = dfprev.copy() if dfprev is not None else None
+        rc = f(_I64(n), _p(p1), _p(tau1), _p(ids), _p(fl1), _p(species),
+               _p(fp1) if fp1 is not None else None, _p(dfp1) if dfp1 is not None else None, _p(fields),
+               C.byref(P), _p(prod), _I64(cp), C.byref(nprod), _p(out), _I64(co), C.byref(nout),
+               _p(first_near), _p(n_events))
+        if rc != 0:
+            raise RuntimeError("orc_mc_cascade failed")
+        if nprod.value <= cp and nout.value <= co:
+            break
+        cap_products, cap_out = 2 * max(cp, nprod.value), 2 * max(co, nout.value)
+    return dict(p=p1, tau=tau1, flags=fl1, fprev=fp1, dfprev=dfp1, products=prod[:nprod.value].copy(),
+                particles=out[:nout.value].copy(), first_near_step=first_near, n_events=n_events)
+

@@ -554,6 +554,21 @@ void orc_uniforms(uint64_t seed, uint64_t id, uint32_t step, uint32_t tag, doubl
     draws(seed, id, step, tag, u);
 }
 
+/* READING (the paper keys no random numbers by particle): the id of a particle created
+ * in a full cascade, a function of its parent (id, tag), the creation step and its member
+ * number (0 emitted photon, 1 electron, 2 positron).  The first two Philox words of the
+ * counter (parent id lo, hi, step, 0x100 | parent tag << 2 | member) under the run's key,
+ * with bit 63 set: the counter's last word lies outside the 0 ... 3 of the step draws, and
+ * the set bit keeps descendants apart from primaries, whose ids are below 2^63. */
+uint64_t orc_child_id(uint64_t seed, uint64_t parent, uint32_t parent_tag, uint32_t step, uint32_t member) {
+    const uint32_t ctr[4] = {(uint32_t)parent, (uint32_t)(parent >> 32), step,
+                             0x100u | ((parent_tag & 3u) << 2) | member};
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    return (1ull << 63) | ((uint64_t)(w[1] & 0x7FFFFFFFu) << 32) | w[0];
+}
+
 /* ------------------------------------------------------------------------- */
 /* Batched entry points (OpenMP over independent elements).                   */
 /* ------------------------------------------------------------------------- */
@@ -663,6 +678,8 @@ typedef struct {
     double near_od;             /* |tau_d| <= near_od * tau0: optical-depth decision near threshold */
     double near_local;          /* |R dt - r| <= near_local * r: local decision near threshold */
     double near_blcfa;          /* relative window of the beyond-LCFA comparisons */
+    int32_t cascade;            /* 1: full cascade, every product is a particle stepped from the next step on */
+    int32_t reserved;
 } orc_run_params;
 
 /* One recorded product. */
@@ -696,7 +713,48 @@ typedef struct {
     uint32_t tag;
     uint8_t flags, species;
     double Fprev[3], dF[3];
+    uint64_t parent;            /* descendants: parent id, creation step and member */
+    uint32_t born, member;
 } orc_state;
+
+/* The particles a lineage has created, in order of creation (growable). */
+typedef struct {
+    orc_state *v;
+    int n, cap;
+} orc_kids;
+
+static orc_state *kid_new(orc_kids *k) {
+    if (k->n == k->cap) {
+        k->cap = k->cap ? 2 * k->cap : 8;
+        k->v = (orc_state *)realloc(k->v, (size_t)k->cap * sizeof(orc_state));
+        if (!k->v) abort();
+    }
+    orc_state *c = &k->v[k->n++];
+    memset(c, 0, sizeof(*c));
+    return c;
+}
+
+/* A created particle: momentum pc, no optical depth yet, BLCFA state zero.  In a cascade it
+ * takes its own id (orc_child_id) and tag 0; otherwise (stepped children of a converted
+ * photon) the parent's id and the member as tag. */
+static void kid_init(orc_state *c, const orc_state *parent, const double pc[3], uint32_t step, uint32_t member,
+                     uint8_t species, const orc_run_params *P) {
+    c->p[0] = pc[0]; c->p[1] = pc[1]; c->p[2] = pc[2];
+    c->tau = -1.0; c->tau0 = 0.0;
+    if (P->cascade) {
+        c->id = orc_child_id(P->seed, parent->id, parent->tag, step, member);
+        c->tag = 0u;
+    } else {
+        c->id = parent->id;
+        c->tag = member;
+    }
+    /* a particle created without momentum does not take part in later steps */
+    c->flags = (uint8_t)((pc[0] != 0.0 || pc[1] != 0.0 || pc[2] != 0.0 ? FL_ALIVE : 0) | FL_JUST_CREATED);
+    c->species = species;
+    c->parent = parent->id;
+    c->born = step;
+    c->member = member;
+}
 
 static void push_product(orc_prod_sink *sink, const double p[3], uint64_t parent_id, uint32_t step,
                          uint32_t parent_tag, uint32_t species, uint32_t member) {
@@ -723,8 +781,7 @@ static double lepton_pmag(double g) { const double q = g * g - 1.0; return q > 0
 
 /* One step of a photon: nonlinear Breit-Wheeler by the optical-depth method. */
 static void step_photon(orc_state *s, const double E[3], const double B[3], uint32_t n,
-                        const orc_run_params *P, orc_prod_sink *sink, orc_lineage_info *info,
-                        orc_state *children, int *n_children) {
+                        const orc_run_params *P, orc_prod_sink *sink, orc_lineage_info *info, orc_kids *kids) {
     double u[4];
     draws(P->seed, s->id, n, s->tag, u);
     if (s->tau < 0.0) { s->tau = -log(u[3]); s->tau0 = s->tau; }
@@ -745,23 +802,15 @@ static void step_photon(orc_state *s, const double E[3], const double B[3], uint
     push_product(sink, pe, s->id, n, s->tag, SP_ELECTRON, 1);
     push_product(sink, pp, s->id, n, s->tag, SP_POSITRON, 2);
     s->flags &= (uint8_t)~FL_ALIVE;                             /* the photon is converted */
-    if (children && P->step_children) {
-        for (int m = 0; m < 2; ++m) {
-            orc_state *c = &children[(*n_children)++];
-            memset(c, 0, sizeof(*c));
-            const double *pc = m == 0 ? pe : pp;
-            c->p[0] = pc[0]; c->p[1] = pc[1]; c->p[2] = pc[2];
-            c->tau = -1.0; c->tau0 = 0.0;
-            c->id = s->id; c->tag = (uint32_t)(m + 1);
-            /* a lepton created without momentum does not take part in later steps */
-            c->flags = (uint8_t)((pc[0] != 0.0 || pc[1] != 0.0 || pc[2] != 0.0 ? FL_ALIVE : 0) | FL_JUST_CREATED);
-            c->species = (uint8_t)(m == 0 ? SP_ELECTRON : SP_POSITRON);
-        }
-    }
+    if (kids)
+        for (int m = 0; m < 2; ++m)
+            kid_init(kid_new(kids), s, m == 0 ? pe : pp, n, (uint32_t)(m + 1),
+                     (uint8_t)(m == 0 ? SP_ELECTRON : SP_POSITRON), P);
 }
 
 /* Recoil of the emitting lepton and the emitted photon for s = u. */
-static void emit_photon(orc_state *s, double gamma, double su, uint32_t n, orc_prod_sink *sink) {
+static void emit_photon(orc_state *s, double gamma, double su, uint32_t n, orc_prod_sink *sink,
+                        const orc_run_params *P, orc_kids *kids) {
     const double pm = sqrt(s->p[0] * s->p[0] + s->p[1] * s->p[1] + s->p[2] * s->p[2]);
     const double nh[3] = {s->p[0] / pm, s->p[1] / pm, s->p[2] / pm};
     const double gph = gamma * su / (1.0 + su);                 /* xi gamma_e */
@@ -771,6 +820,7 @@ static void emit_photon(orc_state *s, double gamma, double su, uint32_t n, orc_p
     const double pm_new = lepton_pmag(gnew);
     collinear(nh, pm_new, pnew);
     push_product(sink, pph, s->id, n, s->tag, SP_PHOTON, 0);
+    if (kids && P->cascade) kid_init(kid_new(kids), s, pph, n, 0u, SP_PHOTON, P);
     s->p[0] = pnew[0]; s->p[1] = pnew[1]; s->p[2] = pnew[2];
     /* READING: a lepton left without momentum is outside the ultrarelativistic regime the
      * rates assume (Sec. 4) and has no direction for collinear emission: it leaves the step */
@@ -779,7 +829,7 @@ static void emit_photon(orc_state *s, double gamma, double su, uint32_t n, orc_p
 
 /* One step of a lepton, LCFA emission by the optical-depth method. */
 static void step_lepton_od(orc_state *s, const double E[3], const double B[3], uint32_t n,
-                           const orc_run_params *P, orc_prod_sink *sink, orc_lineage_info *info) {
+                           const orc_run_params *P, orc_prod_sink *sink, orc_lineage_info *info, orc_kids *kids) {
     double u[4];
     draws(P->seed, s->id, n, s->tag, u);
     if (s->tau < 0.0) { s->tau = -log(u[3]); s->tau0 = s->tau; }
@@ -791,7 +841,7 @@ static void step_lepton_od(orc_state *s, const double E[3], const double B[3], u
     if (!(tn < 0.0)) { s->tau = tn; return; }
     info->n_events++;
     const double su = orc_photon_s(u[1], chi);
-    emit_photon(s, g, su, n, sink);
+    emit_photon(s, g, su, n, sink, P, kids);
     s->tau = -log(u[0]);                                        /* fresh optical depth, Sec. 2 */
     s->tau0 = s->tau;
 }
@@ -804,7 +854,8 @@ static double rej_spectrum(double gg, double ge, double chi) {
 
 /* One step of a lepton, beyond-LCFA emission by the local method (Sec. 5). */
 static void step_lepton_blcfa(orc_state *s, const double E[3], const double B[3], uint32_t n,
-                              const orc_run_params *P, orc_prod_sink *sink, orc_lineage_info *info) {
+                              const orc_run_params *P, orc_prod_sink *sink, orc_lineage_info *info,
+                              orc_kids *kids) {
     blcfa_eval ev;
     const int was_new = (s->flags & FL_JUST_CREATED) != 0;
     uint8_t jc = (uint8_t)was_new;
@@ -843,16 +894,18 @@ static void step_lepton_blcfa(orc_state *s, const double E[3], const double B[3]
     }
     /* READING: without the gate the field is locally constant (or chi is
      * negligible) and the LCFA spectrum applies unchanged. */
-    emit_photon(s, g, su, n, sink);
+    emit_photon(s, g, su, n, sink, P, kids);
 }
 
+/* One step of one particle.  `kids` (may be NULL) receives the particles it creates:
+ * in a cascade every product, otherwise the leptons of a converted photon. */
 static void step_particle(orc_state *s, const double *EB, uint32_t n, const orc_run_params *P,
-                          orc_prod_sink *sink, orc_lineage_info *info, orc_state *children, int *nc) {
+                          orc_prod_sink *sink, orc_lineage_info *info, orc_kids *kids) {
     if (!(s->flags & FL_ALIVE)) return;
     const double *E = EB, *B = EB + 3;
-    if (s->species == SP_PHOTON) step_photon(s, E, B, n, P, sink, info, children, nc);
-    else if (P->lepton_mode != MODE_LCFA_OD) step_lepton_blcfa(s, E, B, n, P, sink, info);
-    else step_lepton_od(s, E, B, n, P, sink, info);
+    if (s->species == SP_PHOTON) step_photon(s, E, B, n, P, sink, info, kids);
+    else if (P->lepton_mode != MODE_LCFA_OD) step_lepton_blcfa(s, E, B, n, P, sink, info, kids);
+    else step_lepton_od(s, E, B, n, P, sink, info, kids);
 }
 
 /* Run `nsteps` steps (numbered step0 ...) for `n` independent primaries.
@@ -879,16 +932,17 @@ int orc_mc_run(int64_t n, double *p, double *tau, const uint64_t *id, const uint
         if (fprev) for (int k = 0; k < 3; ++k) { s.Fprev[k] = fprev[3 * i + k]; s.dF[k] = dfprev[3 * i + k]; }
         orc_prod_sink sink = {0, cap_products, prod, n_products};
         orc_lineage_info info = {-1, 0};
-        orc_state children[2];
-        int nc = 0;
+        orc_kids kids = {NULL, 0, 0};
         for (uint32_t j = 0; j < P->nsteps; ++j) {
             const uint32_t step = P->step0 + j;
             const double *EB = fields + ((size_t)i * P->nsteps + j) * 6;
             /* children created at earlier steps are stepped first (they were
              * created before this step began); then the primary */
-            for (int c = 0; c < nc; ++c) step_particle(&children[c], EB, step, P, &sink, &info, NULL, NULL);
-            step_particle(&s, EB, step, P, &sink, &info, children, &nc);
+            const int nk = kids.n;
+            for (int c = 0; c < nk; ++c) step_particle(&kids.v[c], EB, step, P, &sink, &info, NULL);
+            step_particle(&s, EB, step, P, &sink, &info, P->step_children ? &kids : NULL);
         }
+        free(kids.v);
         p[3 * i] = s.p[0]; p[3 * i + 1] = s.p[1]; p[3 * i + 2] = s.p[2];
         tau[i] = s.tau; flags[i] = s.flags;
         if (fprev) for (int k = 0; k < 3; ++k) { fprev[3 * i + k] = s.Fprev[k]; dfprev[3 * i + k] = s.dF[k]; }
@@ -897,3 +951,80 @@ int orc_mc_run(int64_t n, double *p, double *tau, const uint64_t *id, const uint
     }
     return 0;
 }
+
+/* One particle of a cascade as orc_mc_cascade returns it. */
+typedef struct {
+    double p[3];
+    double tau;
+    uint64_t id, parent_id;
+    int64_t root;               /* index of the primary whose lineage it belongs to */
+    uint32_t step;              /* step of creation */
+    uint32_t member;            /* 0 emitted photon, 1 electron, 2 positron */
+    uint8_t flags, species, pad[6];
+} orc_cascade_particle;
+
+/* Full cascade: as orc_mc_run, and every product (the photon of an emission, the two
+ * leptons of a conversion) is also a particle of the lineage, with its own id
+ * (orc_child_id), no optical depth yet and zero BLCFA state, stepped from the step after
+ * its creation on, in the field of the lineage's primary, and creating particles in turn.
+ * Within a step the particles created at earlier steps are stepped, then the primary; a
+ * particle created during the step waits for the next one.  Primaries carry tag 0.  The
+ * primaries' final state is written in place; every created particle (alive or not) goes
+ * to `out` (atomic counter n_out; entries past cap_out are counted, not written). */
+int orc_mc_cascade(int64_t n, double *p, double *tau, const uint64_t *id, uint8_t *flags, const uint8_t *species,
+                   double *fprev, double *dfprev, const double *fields, const orc_run_params *P,
+                   orc_product *prod, int64_t cap_products, int64_t *n_products,
+                   orc_cascade_particle *out, int64_t cap_out, int64_t *n_out,
+                   int32_t *first_near_step, int32_t *n_events) {
+    if (!P->cascade) return -1;
+    *n_products = 0;
+    *n_out = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < n; ++i) {
+        orc_state s;
+        memset(&s, 0, sizeof(s));
+        s.p[0] = p[3 * i]; s.p[1] = p[3 * i + 1]; s.p[2] = p[3 * i + 2];
+        s.tau = tau[i]; s.tau0 = tau[i] > 0.0 ? tau[i] : 0.0;
+        s.id = id[i]; s.tag = 0u;
+        s.flags = flags[i]; s.species = species[i];
+        if (fprev) for (int k = 0; k < 3; ++k) { s.Fprev[k] = fprev[3 * i + k]; s.dF[k] = dfprev[3 * i + k]; }
+        orc_prod_sink sink = {0, cap_products, prod, n_products};
+        orc_lineage_info info = {-1, 0};
+        orc_kids kids = {NULL, 0, 0};
+        for (uint32_t j = 0; j < P->nsteps; ++j) {
+            const uint32_t step = P->step0 + j;
+            const double *EB = fields + ((size_t)i * P->nsteps + j) * 6;
+            const int nk = kids.n;
+            for (int c = 0; c < nk; ++c) {
+                orc_state t = kids.v[c];                        /* kids.v may move while t steps */
+                step_particle(&t, EB, step, P, &sink, &info, &kids);
+                kids.v[c] = t;
+            }
+            step_particle(&s, EB, step, P, &sink, &info, &kids);
+        }
+        p[3 * i] = s.p[0]; p[3 * i + 1] = s.p[1]; p[3 * i + 2] = s.p[2];
+        tau[i] = s.tau; flags[i] = s.flags;
+        if (fprev) for (int k = 0; k < 3; ++k) { fprev[3 * i + k] = s.Fprev[k]; dfprev[3 * i + k] = s.dF[k]; }
+        first_near_step[i] = info.first_near_step;
+        n_events[i] = info.n_events;
+        for (int c = 0; c < kids.n; ++c) {
+            int64_t k;
+#pragma omp atomic capture
+            k = (*n_out)++;
+            if (k < cap_out) {
+                const orc_state *t = &kids.v[c];
+                orc_cascade_particle *o = &out[k];
+                memset(o, 0, sizeof(*o));
+                o->p[0] = t->p[0]; o->p[1] = t->p[1]; o->p[2] = t->p[2];
+                o->tau = t->tau;
+                o->id = t->id; o->parent_id = t->parent;
+                o->root = i;
+                o->step = t->born; o->member = t->member;
+                o->flags = t->flags; o->species = t->species;
+            }
+        }
+        free(kids.v);
+    }
+    return 0;
+}
+
