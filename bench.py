@@ -340,6 +340,48 @@ def run_ours(args):
         torch.cuda.empty_cache()
         return out_b
 
+    def cascade_leg():
+        """Full cascade: 2^20 electrons of gamma ~ N(1e4, 5%) head-on with the plane wave of
+        a0 = 150, `--cascade-steps` steps in which every product is appended to the population
+        and stepped again.  Timed with CUDA events around the whole run, including the
+        host's count checks between runs of steps and the compactions they trigger."""
+        from paper_2301_07684_gb300 import cascade
+        nc = 1 << 20
+        dc = W.config2(n=nc, seed=rank + 11, dtype=np.float32, a0=150.0, gamma0=1e4)
+        ctx = sfq.Context(ref_len_m=W.REF_LEN, dt=W.DT, precision="fp32", seed=909, device=local)
+        ids = np.arange(nc, dtype=np.uint64) + np.uint64(rank * nc)
+        nsteps_c = args.cascade_steps
+
+        def fresh():
+            return cascade.CascadeRun(ctx, dc, capacity=64 * nc, products_cap=16 * nc, ids=ids)
+
+        warm = fresh()
+        warm.run(0, 2)                                  # builds, loads, first launches
+        torch.cuda.synchronize()
+        del warm
+        r = fresh()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clocks = ClockSampler(local)
+        clocks.start()
+        e0.record()
+        r.run(0, nsteps_c)
+        e1.record()
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1)
+        c = sfq.counters_dict(r.counters)
+        out_c = {"workload": "2^20 e-, gamma0 ~ N(1e4, 5%), head-on plane wave a0 = 150, every product stepped again",
+                 "particles": nc, "final_count": r.count(), "capacity": r.capacity, "steps": nsteps_c,
+                 "value": c["updates"] / (ms * 1e-3), "unit": UNIT, "ms": ms, "updates": c["updates"],
+                 "emitted": c["emitted"], "pairs": c["pairs"], "spawn_dropped": c["spawn_dropped"],
+                 "host_checks": r.host_checks, "compactions": r.compactions, "precision": "fp32-mixed",
+                 "clocks": clk}
+        del r
+        ctx.close()
+        torch.cuda.empty_cache()
+        return out_c
+
     def surrogate_leg():
         """Config 5: the learned inverse-CDF surrogate.  Trained on the GPU (the library's own
         forward/backward/Adam kernels) on 2^22 triples whose targets come from the plain
@@ -524,6 +566,7 @@ def run_ours(args):
     f64 = one_path("fp64", "soa", f64_steps, max(3, min(args.warmup, 3)), with_e2e=False) if "fp64" in legs else None
     trunc = one_path("fp32", "soa", args.steps, args.warmup, with_e2e=False, sampler_k=8) if "trunc" in legs else None
     batched = batched_leg() if "batched" in legs and args.batched_steps > 0 else None
+    casc = cascade_leg() if "cascade" in legs and args.cascade_steps > 0 else None
     surrogate = surrogate_leg() if "surrogate" in legs and args.surrogate_steps > 0 else None
 
     # max over ranks of the headline time
@@ -575,6 +618,7 @@ def run_ours(args):
             "fused_plane_wave": fused,
             "fused_plane_wave_fp64": fused64,
             "batched": batched,
+            "cascade": casc,
             "surrogate": surrogate,
             "events_per_update": main["events_per_update"],
             "device": dev_name,
@@ -675,7 +719,8 @@ def main():
     ap.add_argument("--surrogate-steps", type=int, default=30000,
                     help="training steps of the surrogate leg (0 skips it)")
     ap.add_argument("--fused", type=int, default=1, help="time the fused multi-step plane-wave run (0: skip)")
-    ap.add_argument("--legs", default="config1,pw,fp64,trunc,fused,fused64,batched,surrogate",
+    ap.add_argument("--cascade-steps", type=int, default=100, help="steps of the full-cascade leg")
+    ap.add_argument("--legs", default="config1,pw,fp64,trunc,fused,fused64,batched,cascade,surrogate",
                     help="legs timed beside the headline step (comma list; the headline always runs)")
     ap.add_argument("--shape", default="",
                     help="fixed launch shape 'variant:shape' of the per-step legs (e.g. 2:16) instead of the autotuner")

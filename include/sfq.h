@@ -252,6 +252,44 @@ sfq_status sfq_mc_run(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f,
 sfq_status sfq_mc_run_fused(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, uint32_t step0,
                             uint32_t nsteps, const sfq_products *out, sfq_counters *counters, void *stream);
 
+/* Full cascade (every product is stepped again): `nsteps` steps step0 ... of a population
+ * that grows by its own products.  Each step is the step of sfq_mc_step (Sec. 2 and 4, and
+ * Sec. 5 for beyond-LCFA leptons) over the particles [0, *p->n_dev), and every product of
+ * the step -- the photon of an emission, the two leptons of a conversion -- is also
+ * appended to `p` as a particle: momentum of its record, tau = -1 (drawn at its first step),
+ * flags ALIVE | JUST_CREATED | species with tag 0, BLCFA state 0, k0 and amp copied from the
+ * parent, and its own id: bit 63 over the first two Philox words of the counter
+ * (parent id lo, parent id hi, step, 0x100 | parent tag << 2 | member) under the seed
+ * (member 0 photon, 1 electron, 2 positron).  A particle appended during a step is stepped
+ * from the next step on; after each step *p->n_dev = min(appended total, p->n).  Product
+ * records are written to `out` as by sfq_mc_step.
+ *   p: p->n is the capacity; p->n_dev (device uint64, in/out) the live count; p->id
+ *      (uint64[capacity], written for appended particles, kept below 2^63 for primaries so
+ *      that descendants are told apart) must not be NULL.
+ *   f: SFQ_FIELDS_PLANE_WAVE with k0 (and amp, if not NULL) of capacity elements; the
+ *      cascade writes them for appended particles, so every descendant sees the wave at
+ *      its primary's phase.
+ *   next: device uint64 scratch (the append counter of a step).
+ * Particles that would be appended beyond the capacity are counted in spawn_dropped and
+ * lost; a caller that must lose none keeps 3 * count <= capacity per step (each particle
+ * creates at most two) and makes room with sfq_cascade_compact.  Asynchronous on `stream`;
+ * SFQ_ERR_ARG for invalid descriptors. */
+sfq_status sfq_cascade_run(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, unsigned long long *next,
+                           uint32_t step0, uint32_t nsteps, const sfq_products *out, sfq_counters *counters,
+                           void *stream);
+
+/* Stream compaction of a cascade population: the alive particles of src [0, *src->n_dev)
+ * are moved, in their order, to dst [0, m), and *dst->n_dev = m.  Every per-particle array
+ * moves: momentum, tau, id, flags, the BLCFA state (when src->lepton_model uses it) and the
+ * plane-wave k0 and amp of fsrc -> fdst.  dst->n (its capacity) must be at least src->n, so
+ * a larger dst also grows the population.  The buffers of src and dst must not overlap.
+ * `scratch` (device, 16-byte aligned) holds sfq_cascade_compact_scratch_bytes(src->n) bytes.
+ * Asynchronous on `stream`. */
+size_t sfq_cascade_compact_scratch_bytes(int64_t capacity);
+sfq_status sfq_cascade_compact(sfq_ctx *ctx, const sfq_particles *src, const sfq_fields *fsrc,
+                               const sfq_particles *dst, const sfq_fields *fdst, void *scratch, size_t scratch_bytes,
+                               void *stream);
+
 /* One Boris push of the momenta (Boris 1970), the particle pusher a PIC code runs between
  * Monte Carlo steps; the paper's library leaves it to the host code.  For every alive
  * electron (charge -1) and positron (+1) of `p`, in the fields `f` at `step` (as

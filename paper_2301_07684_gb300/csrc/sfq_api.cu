@@ -109,10 +109,11 @@ sfq_status validate_step(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields 
 }
 
 cudaError_t launch_step(const sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, uint32_t step,
-                        const sfq_products *out, const sfq_spawn *spawn, sfq_counters *counters, cudaStream_t stream) {
+                        const sfq_products *out, const sfq_spawn *spawn, sfq_counters *counters, cudaStream_t stream,
+                        int cascade) {
     if (p->n == 0) return cudaSuccess;
     const int ppt = ctx->step_ppt ? ctx->step_ppt : (ctx->cfg.precision == SFQ_FP64 ? 1 : 2);
-    StepLaunch L{ctx, p, f, step, out, spawn, counters, stream, ctx->step_grid, ppt, ctx->step_variant};
+    StepLaunch L{ctx, p, f, step, out, spawn, counters, stream, ctx->step_grid, ppt, ctx->step_variant, cascade};
     return ctx->cfg.precision == SFQ_FP64 ? launch_step_f64(L) : launch_step_f32(L);
 }
 
@@ -296,6 +297,69 @@ sfq_status sfq_mc_run_fused(sfq_ctx *ctx, const sfq_particles *p, const sfq_fiel
     const cudaError_t e = ctx->cfg.precision == SFQ_FP64 ? sfq::launch_fused_f64(L, nsteps)
                                                          : sfq::launch_fused_f32(L, nsteps);
     return e == cudaSuccess ? SFQ_OK : cuda_fail(ctx, e, "sfq_mc_run_fused");
+}
+
+sfq_status sfq_cascade_run(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, unsigned long long *next,
+                           uint32_t step0, uint32_t nsteps, const sfq_products *out, sfq_counters *counters,
+                           void *stream) {
+    if (!ctx) return SFQ_ERR_ARG;
+    if (!p || !f) return fail(ctx, SFQ_ERR_ARG, "null descriptor");
+    if (f->kind != SFQ_FIELDS_PLANE_WAVE) return fail(ctx, SFQ_ERR_ARG, "cascade: plane-wave fields only");
+    if (!p->n_dev || !aligned8(p->n_dev) || !next || !aligned8(next))
+        return fail(ctx, SFQ_ERR_ARG, "cascade: device count or append counter null or misaligned");
+    if (p->n > 0 && !p->id) return fail(ctx, SFQ_ERR_ARG, "cascade: particle ids required");
+    // the population is its own spawn target
+    sfq_spawn sp{};
+    sp.p = *p;
+    sp.p.n_dev = nullptr;
+    sp.k0 = const_cast<uint32_t *>(f->k0);
+    sp.amp = const_cast<void *>(f->amp);
+    sp.count = next;
+    const sfq_status st = sfq::validate_step(ctx, p, f, out, &sp, counters);
+    if (st != SFQ_OK) return st;
+    if ((uint64_t)step0 + nsteps > 0xFFFFFFFFull) return fail(ctx, SFQ_ERR_ARG, "step0 + nsteps exceeds 2^32 - 1");
+    if (p->n == 0 || nsteps == 0) return SFQ_OK;
+    DeviceGuard g(ctx->device);
+    const cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long *count = const_cast<unsigned long long *>(p->n_dev);
+    cudaError_t e = sfq::launch_cascade_sync(count, next, p->n, true, s);
+    for (uint32_t j = 0; j < nsteps && e == cudaSuccess; ++j) {
+        e = sfq::launch_step(ctx, p, f, step0 + j, out, &sp, counters, s, 1);
+        if (e == cudaSuccess) e = sfq::launch_cascade_sync(count, next, p->n, false, s);
+    }
+    return e == cudaSuccess ? SFQ_OK : cuda_fail(ctx, e, "sfq_cascade_run");
+}
+
+size_t sfq_cascade_compact_scratch_bytes(int64_t capacity) { return sfq::compact_scratch_bytes(capacity); }
+
+sfq_status sfq_cascade_compact(sfq_ctx *ctx, const sfq_particles *src, const sfq_fields *fsrc,
+                               const sfq_particles *dst, const sfq_fields *fdst, void *scratch, size_t scratch_bytes,
+                               void *stream) {
+    if (!ctx) return SFQ_ERR_ARG;
+    if (!src || !fsrc || !dst || !fdst) return fail(ctx, SFQ_ERR_ARG, "null descriptor");
+    if (src->n < 0 || dst->n < src->n) return fail(ctx, SFQ_ERR_ARG, "compaction: dst capacity below src capacity");
+    if (fsrc->kind != SFQ_FIELDS_PLANE_WAVE || fdst->kind != SFQ_FIELDS_PLANE_WAVE)
+        return fail(ctx, SFQ_ERR_ARG, "compaction: plane-wave fields only");
+    if (!src->n_dev || !dst->n_dev || !aligned8(src->n_dev) || !aligned8(dst->n_dev))
+        return fail(ctx, SFQ_ERR_ARG, "compaction: device counts null or misaligned");
+    if (src->lepton_model != dst->lepton_model) return fail(ctx, SFQ_ERR_ARG, "compaction: lepton models differ");
+    if (src->n > 0) {
+        const void *b[] = {src->px, src->py, src->pz, src->tau, src->id, src->flags, fsrc->k0,
+                           dst->px, dst->py, dst->pz, dst->tau, dst->id, dst->flags, fdst->k0};
+        for (const void *q : b)
+            if (!q || !aligned16(q)) return fail(ctx, SFQ_ERR_ARG, "compaction: buffer null or misaligned");
+        if (!fsrc->amp != !fdst->amp) return fail(ctx, SFQ_ERR_ARG, "compaction: amp given on one side only");
+        if (src->lepton_model != SFQ_LEPTON_LCFA_OD)
+            for (int k = 0; k < 3; ++k)
+                if (!src->fprev[k] || !src->dfprev[k] || !dst->fprev[k] || !dst->dfprev[k])
+                    return fail(ctx, SFQ_ERR_ARG, "compaction: beyond-LCFA state arrays null");
+    }
+    if (!scratch || !aligned16(scratch) || scratch_bytes < sfq::compact_scratch_bytes(src->n))
+        return fail(ctx, SFQ_ERR_ARG, "compaction: scratch null, misaligned or too small");
+    DeviceGuard g(ctx->device);
+    const cudaError_t e = sfq::launch_compact(ctx->cfg.precision, *src, *fsrc, *dst, *fdst, scratch,
+                                              (cudaStream_t)stream);
+    return e == cudaSuccess ? SFQ_OK : cuda_fail(ctx, e, "sfq_cascade_compact");
 }
 
 sfq_status sfq_push(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, uint32_t step, double dt,

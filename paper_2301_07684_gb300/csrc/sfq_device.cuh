@@ -36,6 +36,17 @@ __device__ __forceinline__ u4 draws(uint64_t seed, uint64_t id, uint32_t step, u
                          (uint32_t)(seed >> 32));
 }
 
+// Id of a particle created in a full cascade: bit 63 over the first two words of the
+// counter (parent id lo, hi, step, 0x100 | parent tag << 2 | member) under the run's key.
+// The counter's last word is outside the 0 ... 3 of the step draws; the set bit keeps
+// descendants apart from primaries (ids below 2^63).
+__device__ __forceinline__ uint64_t child_id(uint64_t seed, uint64_t parent, uint32_t parent_tag, uint32_t step,
+                                             uint32_t member) {
+    const u4 w = philox4x32_10((uint32_t)parent, (uint32_t)(parent >> 32), step,
+                               0x100u | ((parent_tag & 3u) << 2) | member, (uint32_t)seed, (uint32_t)(seed >> 32));
+    return (1ull << 63) | ((uint64_t)(w.w[1] & 0x7FFFFFFFu) << 32) | (uint64_t)w.w[0];
+}
+
 // u = (floor(w / 2^9) + 1/2) 2^-23: exact in binary32 and binary64, in [2^-24, 1 - 2^-24].
 template <typename T>
 __device__ __forceinline__ T uniform(uint32_t w) {

@@ -61,6 +61,7 @@ struct StepLaunch {
     int grid;
     int ppt;
     int variant;
+    int cascade = 0;         // 1: every product is also spawned (full cascade)
 };
 
 cudaError_t launch_rate_f32(const RateLaunch &, bool pair);
@@ -88,7 +89,14 @@ cudaError_t launch_fused_f64(const StepLaunch &, uint32_t nsteps);
 sfq_status validate_step(sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, const sfq_products *out,
                          const sfq_spawn *spawn, const sfq_counters *counters);
 cudaError_t launch_step(const sfq_ctx *ctx, const sfq_particles *p, const sfq_fields *f, uint32_t step,
-                        const sfq_products *out, const sfq_spawn *spawn, sfq_counters *counters, cudaStream_t stream);
+                        const sfq_products *out, const sfq_spawn *spawn, sfq_counters *counters, cudaStream_t stream,
+                        int cascade = 0);
+// Full cascade (sfq_cascade.cu): the count commit around a step and the stream compaction.
+cudaError_t launch_cascade_sync(unsigned long long *count, unsigned long long *next, int64_t cap, bool begin,
+                                cudaStream_t s);
+size_t compact_scratch_bytes(int64_t capacity);
+cudaError_t launch_compact(int precision, const sfq_particles &src, const sfq_fields &fsrc, const sfq_particles &dst,
+                           const sfq_fields &fdst, void *scratch, cudaStream_t s);
 // Dynamic shared-memory attributes of every kernel shape (before graph capture).
 cudaError_t prepare_step_f32();
 cudaError_t prepare_step_f64();

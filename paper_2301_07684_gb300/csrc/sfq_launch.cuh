@@ -171,7 +171,7 @@ static cudaError_t launch_step_t(const StepLaunch &L) {
     const int cw = TRUNC ? TRUNC_CW : ((L.ppt == 8 || L.ppt == 16 || L.ppt == 20) ? L.ppt : 16);
     const int tile = cw * (sizeof(T) == 4 ? 64 : 32);
     // the beyond-LCFA model runs on the warp-streaming kernel (its state is read directly)
-    const bool tma = p.lepton_model == SFQ_LEPTON_LCFA_OD &&
+    const bool tma = !L.cascade && p.lepton_model == SFQ_LEPTON_LCFA_OD &&
                      (L.variant == 2 || (L.variant == 0 && p.n >= (int64_t)tile * ctx->num_sms));
     if (tma) {
         void (*kern)(const StepArgs<T>) = nullptr;
@@ -205,7 +205,10 @@ static cudaError_t launch_step_t(const StepLaunch &L) {
         return cudaGetLastError();
     }
     void (*kern)(const StepArgs<T>) = nullptr;
-    if constexpr (TRUNC) {
+    if (L.cascade) {
+        // the full cascade (plane-wave fields only) runs its own instance of this kernel
+        kern = mc_step_kernel<T, FK_PW, TRUNC ? TRUNC_PPT : 2, TRUNC, true>;
+    } else if constexpr (TRUNC) {
         kern = pw ? mc_step_kernel<T, FK_PW, TRUNC_PPT, true> : mc_step_kernel<T, FK_SOA, TRUNC_PPT, true>;
     } else {
         switch ((pw ? 10 : 0) + L.ppt) {
@@ -217,7 +220,7 @@ static cudaError_t launch_step_t(const StepLaunch &L) {
             default: kern = mc_step_kernel<T, FK_SOA, 2>; break;
         }
     }
-    const int ppt = TRUNC ? TRUNC_PPT : L.ppt;
+    const int ppt = TRUNC ? TRUNC_PPT : (L.cascade ? 2 : L.ppt);
     int grid = L.grid;
     if (grid <= 0) {
         // one wave of resident blocks: a multiple of the SM count

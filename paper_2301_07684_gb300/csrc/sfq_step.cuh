@@ -334,7 +334,7 @@ __device__ __forceinline__ void reserve_records(unsigned long long *ocount, unsi
 // global atomic per batch, before the sampling when every record count is known up
 // front (no beyond-LCFA lane, whose emission may be rejected), so that the atomic's
 // latency overlaps the sampling.
-template <typename T, bool TRUNC = false>
+template <typename T, bool TRUNC = false, bool CASC = false>
 __device__ __forceinline__ void process_events_core(const StepArgs<T> &a, uint32_t step, int64_t ei, T eg, T echi,
                                                     T e_aux, T px, T py, T pz, uint8_t fl, bool valid, Cnt &c,
                                                     EvOut<T> &o) {
@@ -343,7 +343,8 @@ __device__ __forceinline__ void process_events_core(const StepArgs<T> &a, uint32
     const bool maybe = valid && !photon && !(e_aux < (T)0);        // beyond-LCFA: may be rejected
     const bool late = __any_sync(0xFFFFFFFFu, maybe);
     int nprod = valid ? (photon ? 2 : 1) : 0;
-    int nspawn = photon && a.scount ? 2 : 0;
+    // spawned particles: the pair of a converted photon; in a cascade also the emitted photon
+    int nspawn = a.scount ? (photon ? 2 : (CASC ? nprod : 0)) : 0;
     unsigned long long bp = 0, bs = 0;
     if (!late) reserve_records(a.ocount, a.scount, nprod, nspawn, bp, bs);
     T xa = 0, xb = 0;
@@ -380,6 +381,7 @@ __device__ __forceinline__ void process_events_core(const StepArgs<T> &a, uint32
                 ++c.v[C_EMIT];
             } else {
                 nprod = 0;
+                nspawn = 0;
                 ++c.v[C_REJ];
             }
         }
@@ -410,10 +412,10 @@ __device__ __forceinline__ void process_events_core(const StepArgs<T> &a, uint32
                 if (s < (unsigned long long)a.scap) {
                     a.spx[s] = nx * pmag; a.spy[s] = ny * pmag; a.spz[s] = nz * pmag;
                     a.stau[s] = -1.0;
-                    a.sid[s] = id;
+                    a.sid[s] = CASC ? child_id(a.seed, id, tag, step, (uint32_t)(m + 1)) : id;
                     a.sflags[s] = (uint8_t)((pmag > (T)0 ? SFQ_ALIVE : 0) | SFQ_JUST_CREATED |
                                             ((m == 0 ? SFQ_ELECTRON : SFQ_POSITRON) << SFQ_SPECIES_SHIFT) |
-                                            ((m + 1) << SFQ_TAG_SHIFT));
+                                            (CASC ? 0 : (m + 1) << SFQ_TAG_SHIFT));
                     if (a.sfp[0]) {
 #pragma unroll
                         for (int d3 = 0; d3 < 3; ++d3) { a.sfp[d3][s] = (T)0; a.sdf[d3][s] = (T)0; }
@@ -442,6 +444,25 @@ __device__ __forceinline__ void process_events_core(const StepArgs<T> &a, uint32
         } else {
             ++c.v[C_DROP];
         }
+        if (CASC && nspawn) {
+            // full cascade: the photon is also a particle, stepped from the next step on
+            const unsigned long long sj = bs;
+            if (sj < (unsigned long long)a.scap) {
+                a.spx[sj] = nx * gph; a.spy[sj] = ny * gph; a.spz[sj] = nz * gph;
+                a.stau[sj] = -1.0;
+                a.sid[sj] = child_id(a.seed, id, tag, step, 0u);
+                a.sflags[sj] = (uint8_t)((gph > (T)0 ? SFQ_ALIVE : 0) | SFQ_JUST_CREATED |
+                                         (SFQ_PHOTON << SFQ_SPECIES_SHIFT));
+                if (a.sfp[0]) {
+#pragma unroll
+                    for (int d3 = 0; d3 < 3; ++d3) { a.sfp[d3][sj] = (T)0; a.sdf[d3][sj] = (T)0; }
+                }
+                if (a.sk0) a.sk0[sj] = a.k0[ei];
+                if (a.samp) a.samp[sj] = a.amp ? a.amp[ei] : a.amp0;
+            } else {
+                ++c.v[C_SDROP];
+            }
+        }
         o.px = nx * pnew; o.py = ny * pnew; o.pz = nz * pnew;
         o.what = 1;
         if (xb > (T)0) {                                        // fresh optical depth, word 0 (Sec. 2)
@@ -459,11 +480,11 @@ __device__ __forceinline__ void process_events_core(const StepArgs<T> &a, uint32
 
 // process_events_core at the launch's step with the parent's new state stored to the
 // population in global memory.
-template <typename T, bool TRUNC = false>
+template <typename T, bool TRUNC = false, bool CASC = false>
 __device__ __forceinline__ void process_events(const StepArgs<T> &a, int64_t ei, T eg, T echi, T e_aux, T px,
                                                T py, T pz, uint8_t fl, bool valid, Cnt &c) {
     EvOut<T> o;
-    process_events_core<T, TRUNC>(a, a.step, ei, eg, echi, e_aux, px, py, pz, fl, valid, c, o);
+    process_events_core<T, TRUNC, CASC>(a, a.step, ei, eg, echi, e_aux, px, py, pz, fl, valid, c, o);
     if (o.what & 1) { a.px[ei] = o.px; a.py[ei] = o.py; a.pz[ei] = o.pz; }
     if (o.what & 2) a.tau[ei] = o.tau;
     if (o.what & 4) a.flags[ei] = o.fl;
@@ -572,7 +593,8 @@ __device__ __forceinline__ void step_lepton_pair(const StepArgs<float> &a, const
 // Each warp streams chunks of 32*PPT particles and compacts event lanes into a
 // warp-private ring in shared memory; a full batch of 32 events is sampled by the
 // whole warp.  No block-wide barrier inside the loop.
-template <typename T, int FK, int PPT, bool TRUNC = false>
+// CASC: the full-cascade instance (every product is also spawned, with its own id).
+template <typename T, int FK, int PPT, bool TRUNC = false, bool CASC = false>
 __global__ void __launch_bounds__(STEP_BS, SFQ_STEP_MINB) mc_step_kernel(const StepArgs<T> a) {
     using Q = L<T>;
     constexpr int WARPS = STEP_BS / 32;
@@ -635,7 +657,7 @@ __global__ void __launch_bounds__(STEP_BS, SFQ_STEP_MINB) mc_step_kernel(const S
             const QEntryX<T> e = q[(head + lane) & (QS - 1)];
             __syncwarp();
             head += 32;
-            process_events<T, TRUNC>(a, e.i, e.g, e.chi, e.aux, a.px[e.i], a.py[e.i], a.pz[e.i], a.flags[e.i], true,
+            process_events<T, TRUNC, CASC>(a, e.i, e.g, e.chi, e.aux, a.px[e.i], a.py[e.i], a.pz[e.i], a.flags[e.i], true,
                                      c);
         }
     }
@@ -645,7 +667,7 @@ __global__ void __launch_bounds__(STEP_BS, SFQ_STEP_MINB) mc_step_kernel(const S
         const unsigned nv = tail - head;
         const QEntryX<T> e = q[(head + lane) & (QS - 1)];
         const bool v = (unsigned)lane < nv;
-        process_events<T, TRUNC>(a, e.i, e.g, e.chi, e.aux, v ? a.px[e.i] : (T)0, v ? a.py[e.i] : (T)0,
+        process_events<T, TRUNC, CASC>(a, e.i, e.g, e.chi, e.aux, v ? a.px[e.i] : (T)0, v ? a.py[e.i] : (T)0,
                           v ? a.pz[e.i] : (T)0, v ? a.flags[e.i] : (uint8_t)0, v, c);
     }
     flush_counters(c, a.counters);

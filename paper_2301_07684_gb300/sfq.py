@@ -134,6 +134,14 @@ def lib():
         L.sfq_mlp_sample_pair_xi.argtypes = [vp, i64, vp, vp, vp, vp, C.c_int32, vp, vp]
         L.sfq_mlp_sample_pair_xi.restype = st
         L.sfq_mlp_sample_photon_xi.restype = st
+        L.sfq_cascade_run.argtypes = [vp, C.POINTER(Particles), C.POINTER(Fields), vp, u32, u32,
+                                      C.POINTER(Products), vp, vp]
+        L.sfq_cascade_run.restype = st
+        L.sfq_cascade_compact_scratch_bytes.argtypes = [i64]
+        L.sfq_cascade_compact_scratch_bytes.restype = C.c_size_t
+        L.sfq_cascade_compact.argtypes = [vp, C.POINTER(Particles), C.POINTER(Fields), C.POINTER(Particles),
+                                          C.POINTER(Fields), vp, C.c_size_t, vp]
+        L.sfq_cascade_compact.restype = st
         L.sfq_set_step_shape.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
         L.sfq_set_step_shape.restype = st
         L.sfq_version.restype = C.c_char_p
@@ -148,6 +156,7 @@ EXPORTED = ["sfq_init", "sfq_finalize", "sfq_last_error", "sfq_constants", "sfq_
             "sfq_mlp_num_params", "sfq_mlp_create", "sfq_mlp_destroy", "sfq_mlp_get_params", "sfq_mlp_set_params",
             "sfq_mlp_loss_grad", "sfq_mlp_train", "sfq_mlp_predict_lnw", "sfq_mlp_plain_targets", "sfq_mlp_calibrate",
             "sfq_mlp_sample_photon_xi", "sfq_mlp_create_pair", "sfq_mlp_sample_pair_xi",
+            "sfq_cascade_run", "sfq_cascade_compact_scratch_bytes", "sfq_cascade_compact",
             "sfq_version"]
 
 
@@ -284,6 +293,22 @@ class Context:
         P, F, O = particles.descriptor(), fields.descriptor(), products.descriptor()
         self._check(lib().sfq_mc_run_fused(self._h, C.byref(P), C.byref(F), step0, nsteps, C.byref(O),
                                            _ptr(counters), _stream()), "sfq_mc_run_fused")
+
+    def cascade_run(self, particles: "ParticleBuffers", fields: "FieldSource", next_count, step0: int, nsteps: int,
+                    products: "ProductBuffers", counters=None):
+        """nsteps steps of a population that grows by its own products (particles.n_dev holds the
+        live count, particles.n the capacity; next_count is a device scratch counter)."""
+        P, F, O = particles.descriptor(), fields.descriptor(), products.descriptor()
+        self._check(lib().sfq_cascade_run(self._h, C.byref(P), C.byref(F), _ptr(next_count), step0, nsteps,
+                                          C.byref(O), _ptr(counters), _stream()), "sfq_cascade_run")
+
+    def cascade_compact(self, src: "ParticleBuffers", fsrc: "FieldSource", dst: "ParticleBuffers",
+                        fdst: "FieldSource", scratch):
+        """Moves the alive particles of src, in order, to the front of dst (dst.n_dev = their number)."""
+        S, FS, D, FD = src.descriptor(), fsrc.descriptor(), dst.descriptor(), fdst.descriptor()
+        self._check(lib().sfq_cascade_compact(self._h, C.byref(S), C.byref(FS), C.byref(D), C.byref(FD),
+                                              _ptr(scratch), scratch.numel() * scratch.element_size(), _stream()),
+                    "sfq_cascade_compact")
 
     def push(self, particles: "ParticleBuffers", fields: "FieldSource", step: int, dt: float):
         """One Boris push of the leptons' momenta in the fields at `step`."""
@@ -429,6 +454,10 @@ class Surrogate:
 
 def sort_scratch_bytes(n):
     return int(lib().sfq_sort_scratch_bytes(n))
+
+
+def cascade_compact_scratch_bytes(capacity):
+    return int(lib().sfq_cascade_compact_scratch_bytes(capacity))
 
 
 # --- buffers -------------------------------------------------------------------
