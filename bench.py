@@ -382,6 +382,37 @@ def run_ours(args):
         torch.cuda.empty_cache()
         return out_c
 
+    def evaluator_leg():
+        """The table entry points (photon rate, photon and pair samplers) over 2^24 binary32
+        elements with each evaluator of the fitted tables: Horner on the monomial pieces,
+        Clenshaw on the same pieces in the Chebyshev basis."""
+        ne = 1 << 24
+        ctx = sfq.Context(ref_len_m=W.REF_LEN, dt=W.DT, precision="fp32", seed=5, device=local)
+        g = np.random.default_rng(rank + 3)
+        dev = lambda a: torch.as_tensor(a.astype(np.float32)).to(device)
+        chi, gam, r = dev(10.0 ** g.uniform(-3, 3, ne)), dev(10.0 ** g.uniform(1, 5, ne)), dev(g.uniform(1e-7, 1 - 1e-7, ne))
+        res = {}
+        for name, kind in (("horner", sfq.SFQ_EVAL_HORNER), ("clenshaw", sfq.SFQ_EVAL_CLENSHAW)):
+            ctx.set_evaluator(kind)
+            row = {}
+            for what, fn in (("photon_rate", lambda: ctx.photon_rate(gam, chi)),
+                             ("photon_xi", lambda: ctx.sample_photon_xi(chi, r)),
+                             ("pair_xi", lambda: ctx.sample_pair_xi(chi, r))):
+                for _ in range(3):
+                    fn()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(10):
+                    fn()
+                e1.record()
+                torch.cuda.synchronize()
+                row[what] = ne * 10 / (e0.elapsed_time(e1) * 1e-3)
+            res[name] = row
+        ctx.close()
+        torch.cuda.empty_cache()
+        return {"elements": ne, "unit": "elements/s", "precision": "fp32", **res}
+
     def surrogate_leg():
         """Config 5: the learned inverse-CDF surrogate.  Trained on the GPU (the library's own
         forward/backward/Adam kernels) on 2^22 triples whose targets come from the plain
@@ -567,6 +598,7 @@ def run_ours(args):
     trunc = one_path("fp32", "soa", args.steps, args.warmup, with_e2e=False, sampler_k=8) if "trunc" in legs else None
     batched = batched_leg() if "batched" in legs and args.batched_steps > 0 else None
     casc = cascade_leg() if "cascade" in legs and args.cascade_steps > 0 else None
+    evaluators = evaluator_leg() if "evaluators" in legs else None
     surrogate = surrogate_leg() if "surrogate" in legs and args.surrogate_steps > 0 else None
 
     # max over ranks of the headline time
@@ -619,6 +651,7 @@ def run_ours(args):
             "fused_plane_wave_fp64": fused64,
             "batched": batched,
             "cascade": casc,
+            "evaluators": evaluators,
             "surrogate": surrogate,
             "events_per_update": main["events_per_update"],
             "device": dev_name,
@@ -720,7 +753,7 @@ def main():
                     help="training steps of the surrogate leg (0 skips it)")
     ap.add_argument("--fused", type=int, default=1, help="time the fused multi-step plane-wave run (0: skip)")
     ap.add_argument("--cascade-steps", type=int, default=100, help="steps of the full-cascade leg")
-    ap.add_argument("--legs", default="config1,pw,fp64,trunc,fused,fused64,batched,cascade,surrogate",
+    ap.add_argument("--legs", default="config1,pw,fp64,trunc,fused,fused64,batched,cascade,evaluators,surrogate",
                     help="legs timed beside the headline step (comma list; the headline always runs)")
     ap.add_argument("--shape", default="",
                     help="fixed launch shape 'variant:shape' of the per-step legs (e.g. 2:16) instead of the autotuner")

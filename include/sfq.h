@@ -329,6 +329,18 @@ sfq_status sfq_set_pair_rate_cutoff(sfq_ctx *ctx, double chi_min);
 sfq_status sfq_set_sampler_coefficients(sfq_ctx *ctx, int32_t k);
 sfq_status sfq_sampler_coefficients(const sfq_ctx *ctx, int32_t *n, int32_t *k);
 
+/* Evaluator of the fitted tables behind sfq_photon_rate, sfq_pair_rate, sfq_sample_photon_xi
+ * and sfq_sample_pair_xi.  SFQ_EVAL_HORNER (default): every piece as a polynomial in the
+ * monomial basis, evaluated by Horner's rule.  SFQ_EVAL_CLENSHAW: the same pieces converted
+ * to the Chebyshev basis (on the host, in binary64, then rounded to the context's precision)
+ * and evaluated by Clenshaw's recurrence, the layout of the paper's own piecewise Chebyshev
+ * fits (Sec. 4), offered as a comparison; results agree with Horner's to rounding.  The
+ * Monte Carlo step kernels always use Horner.  SFQ_EVAL_CLENSHAW needs the full sampler
+ * tables (sfq_set_sampler_coefficients with k = n), else SFQ_ERR_ARG; the first switch to it
+ * allocates and uploads the Chebyshev tables (synchronously). */
+enum { SFQ_EVAL_HORNER = 0, SFQ_EVAL_CLENSHAW = 1 };
+sfq_status sfq_set_evaluator(sfq_ctx *ctx, int32_t kind);
+
 /* Autotuner: times every launch shape of sfq_mc_step (kernel variant, particles per lane
  * or warps per block) on a copy of up to `sample_n` particles of `p` (the caller's state
  * is not modified; the copy lives in temporary device memory for the duration of the

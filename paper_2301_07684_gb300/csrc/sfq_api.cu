@@ -188,8 +188,9 @@ void sfq_finalize(sfq_ctx *ctx) {
     {
         DeviceGuard g(ctx->device);
         sfq::release_graphs(ctx);
-        void *ptrs[8] = {ctx->d_nlc_rate, ctx->d_nbw_rate, ctx->d_nlc_inv, ctx->d_nbw_inv, ctx->d_k23, ctx->d_ki13,
-                         ctx->d_nlc_inv_r, ctx->d_nbw_inv_r};
+        void *ptrs[12] = {ctx->d_nlc_rate, ctx->d_nbw_rate, ctx->d_nlc_inv, ctx->d_nbw_inv, ctx->d_k23, ctx->d_ki13,
+                          ctx->d_nlc_inv_r, ctx->d_nbw_inv_r, ctx->d_nlc_rate_ch, ctx->d_nbw_rate_ch,
+                          ctx->d_nlc_inv_ch, ctx->d_nbw_inv_ch};
         for (void *p : ptrs)
             if (p) cudaFree(p);
     }
@@ -214,8 +215,11 @@ static sfq_status rate_common(sfq_ctx *ctx, int64_t n, const void *gamma, const 
     if (!aligned16(gamma) || !aligned16(chi) || !aligned16(rate) || (counters && !aligned8(counters)))
         return fail(ctx, SFQ_ERR_ARG, "misaligned buffer (16 bytes required)");
     DeviceGuard g(ctx->device);
-    sfq::RateLaunch L{n, gamma, chi, rate, pair ? ctx->d_nbw_rate : ctx->d_nlc_rate, ctx->pref, counters,
-                      (cudaStream_t)stream, grid_for(ctx, n, 256 * 4), ctx->pair_chi_min};
+    const bool ch = ctx->eval == SFQ_EVAL_CLENSHAW;
+    const void *table = ch ? (pair ? ctx->d_nbw_rate_ch : ctx->d_nlc_rate_ch)
+                           : (pair ? ctx->d_nbw_rate : ctx->d_nlc_rate);
+    sfq::RateLaunch L{n, gamma, chi, rate, table, ctx->pref, counters, (cudaStream_t)stream,
+                      grid_for(ctx, n, 256 * 4), ctx->pair_chi_min, ch ? 1 : 0};
     const cudaError_t e = is_fp64(ctx) ? sfq::launch_rate_f64(L, pair) : sfq::launch_rate_f32(L, pair);
     return e == cudaSuccess ? SFQ_OK : cuda_fail(ctx, e, pair ? "sfq_pair_rate" : "sfq_photon_rate");
 }
@@ -386,10 +390,44 @@ sfq_status sfq_set_pair_rate_cutoff(sfq_ctx *ctx, double chi_min) {
     return SFQ_OK;
 }
 
+sfq_status sfq_set_evaluator(sfq_ctx *ctx, int32_t kind) {
+    if (!ctx) return SFQ_ERR_ARG;
+    if (kind != SFQ_EVAL_HORNER && kind != SFQ_EVAL_CLENSHAW) return fail(ctx, SFQ_ERR_ARG, "unknown evaluator");
+    if (kind == SFQ_EVAL_CLENSHAW && ctx->inv_tr > 0)
+        return fail(ctx, SFQ_ERR_ARG, "the Clenshaw evaluator reads the full tables: set n coefficients first");
+    if (kind == SFQ_EVAL_CLENSHAW && !ctx->d_nlc_rate_ch) {
+        DeviceGuard g(ctx->device);
+        const int prec = ctx->cfg.precision;
+        const std::vector<unsigned char> h[4] = {sfq::chebyshev_rate_table(prec, false),
+                                                 sfq::chebyshev_rate_table(prec, true),
+                                                 sfq::chebyshev_inv_table(prec, false),
+                                                 sfq::chebyshev_inv_table(prec, true)};
+        void *d[4] = {nullptr, nullptr, nullptr, nullptr};
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+            e = cudaMalloc(&d[k], h[k].size());
+            if (e == cudaSuccess) e = cudaMemcpy(d[k], h[k].data(), h[k].size(), cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess) {
+            for (void *q : d)
+                if (q) cudaFree(q);
+            return cuda_fail(ctx, e, "sfq_set_evaluator");
+        }
+        ctx->d_nlc_rate_ch = d[0];
+        ctx->d_nbw_rate_ch = d[1];
+        ctx->d_nlc_inv_ch = d[2];
+        ctx->d_nbw_inv_ch = d[3];
+    }
+    ctx->eval = kind;
+    return SFQ_OK;
+}
+
 sfq_status sfq_set_sampler_coefficients(sfq_ctx *ctx, int32_t k) {
     if (!ctx) return SFQ_ERR_ARG;
     const int n = sfq::inv_coefficients(ctx->cfg.precision);
     if (k < n - 2 || k > n) return fail(ctx, SFQ_ERR_ARG, "coefficients per variable must be n, n - 1 or n - 2");
+    if (k < n && ctx->eval == SFQ_EVAL_CLENSHAW)
+        return fail(ctx, SFQ_ERR_ARG, "truncated samplers need the Horner evaluator");
     const int tr = n - k;
     DeviceGuard g(ctx->device);
     void *nlc = nullptr, *nbw = nullptr;

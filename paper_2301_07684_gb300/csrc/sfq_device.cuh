@@ -214,6 +214,39 @@ __device__ __forceinline__ T horner2(const T *__restrict__ c, T x, T y) {
     return acc;
 }
 
+// sum_ab c[a*ROW+b] T_a(x) T_b(y), a <= DX, b <= DY (Chebyshev pieces): Clenshaw's
+// recurrence in y for each row a, then in x over the rows' values.  Same row layout as
+// horner2.
+template <int DX, int DY, typename T>
+__device__ __forceinline__ T clenshaw2(const T *__restrict__ c, T x, T y) {
+    constexpr int ROW = padded_row(DY + 1, (int)sizeof(T));
+    constexpr int V = 16 / (int)sizeof(T);
+    const T x2 = x + x, y2 = y + y;
+    T ob1 = (T)0, ob2 = (T)0;                 // the recurrence in x
+#pragma unroll
+    for (int a = DX; a >= 0; --a) {
+        T co[ROW];
+#pragma unroll
+        for (int k = 0; k < ROW / V; ++k) ldg_vec(c + a * ROW + k * V, co + k * V);
+        T b1 = (T)0, b2 = (T)0;
+#pragma unroll
+        for (int b = DY; b >= 1; --b) {
+            const T b0 = fma(y2, b1, co[b] - b2);
+            b2 = b1;
+            b1 = b0;
+        }
+        const T ra = fma(y, b1, co[0] - b2);     // the row's series at y
+        if (a >= 1) {
+            const T o0 = fma(x2, ob1, ra - ob2);
+            ob2 = ob1;
+            ob1 = o0;
+        } else {
+            return fma(x, ob1, ra - ob2);
+        }
+    }
+    return (T)0;
+}
+
 // ---------------------------------------------------------------------------
 // Square root and reciprocal square root from the hardware estimate plus one Newton
 // step (about 1 ulp in binary32; the binary64 versions use the library functions).

@@ -23,6 +23,9 @@ struct sfq_ctx {
     double pair_chi_min = 0.01;   // NBW rate is zero below this chi (sfq_set_pair_rate_cutoff)
     int inv_tr = 0;               // inverse-CDF coefficients dropped per variable (sfq_set_sampler_coefficients)
     void *d_nlc_inv_r = nullptr, *d_nbw_inv_r = nullptr;   // the truncated tables when inv_tr > 0
+    int eval = 0;                 // SFQ_EVAL_HORNER or SFQ_EVAL_CLENSHAW (sfq_set_evaluator)
+    void *d_nlc_rate_ch = nullptr, *d_nbw_rate_ch = nullptr;   // Chebyshev pieces (Clenshaw evaluator)
+    void *d_nlc_inv_ch = nullptr, *d_nbw_inv_ch = nullptr;
     std::string err;
 };
 
@@ -39,6 +42,7 @@ struct RateLaunch {
     cudaStream_t stream;
     int grid;
     double pair_chi_min;
+    int cheb = 0;            // `table` holds Chebyshev pieces (Clenshaw evaluator)
 };
 struct SampleLaunch {
     int64_t n;
@@ -114,6 +118,10 @@ HostTables host_tables(int precision);
 // Inverse-CDF table with every piece's (n x n) coefficients truncated to (n - tr) x (n - tr)
 // in the Chebyshev basis, rows padded to 16 bytes (sfq_tables_host.cu).
 std::vector<unsigned char> truncated_inv_table(int precision, bool pair, int tr);
+// The rate and inverse-CDF tables with every piece in the Chebyshev basis (same piece grid;
+// inverse-CDF rows padded to 16 bytes), for the Clenshaw comparison evaluator.
+std::vector<unsigned char> chebyshev_rate_table(int precision, bool pair);
+std::vector<unsigned char> chebyshev_inv_table(int precision, bool pair);
 int inv_coefficients(int precision);   // n of the context's inverse-CDF tables
 
 }  // namespace sfq

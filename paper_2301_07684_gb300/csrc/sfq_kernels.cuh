@@ -108,15 +108,38 @@ __device__ __forceinline__ double horner_smem(const double *c, double x) {
     return acc;
 }
 
+// Clenshaw's recurrence for sum_a c_a T_a(x), the Chebyshev series of a piece on [-1, 1]:
+// b_a = c_a + 2x b_(a+1) - b_(a+2) from a = DEG down to 1, then c_0 + x b_1 - b_2.  The
+// comparison evaluator of the tables in the Chebyshev basis (two operations per
+// coefficient against Horner's one on the same piece in the monomial basis).
+template <int DEG, int STRIDE, typename T>
+__device__ __forceinline__ T clenshaw_smem(const T *c, T x) {
+    T co[STRIDE];
+#pragma unroll
+    for (int k = 0; k < STRIDE; ++k) co[k] = c[k];
+    const T x2 = x + x;
+    T b1 = (T)0, b2 = (T)0;
+#pragma unroll
+    for (int a = DEG; a >= 1; --a) {
+        const T b0 = fma(x2, b1, co[a] - b2);
+        b2 = b1;
+        b1 = b0;
+    }
+    return fma(x, b1, co[0] - b2);
+}
+
 // ---------------------------------------------------------------------------
-// Fitted functions.
+// Fitted functions.  CH = true evaluates tables that hold every piece in the Chebyshev
+// basis by Clenshaw's recurrence (the comparison evaluator); the default is Horner on the
+// monomial pieces.
 // W~_rad(chi) (Eq. wtilde); `c` is the rate table (shared memory in the step kernel).
-template <typename T>
+template <typename T, bool CH = false>
 __device__ __forceinline__ T wtilde_rad(const T *c, T chi, bool &oor) {
     using Q = L<T>;
     constexpr int ST = RateSmem<T>::NLC_STRIDE;
     T x;
     const int p = octave_piece<T, Q::NLC_ELO, Q::NLC_EHI, Q::NLC_SUB, Q::NLC_LOW, Q::NLC_SUBLOW>(chi, x, oor);
+    if (CH) return clenshaw_smem<Q::NLC_DEG, ST>(c + p * ST, x);
     return horner_smem<Q::NLC_DEG, ST>(c + p * ST, x);
 }
 
@@ -135,20 +158,20 @@ __device__ __forceinline__ double exp_m83(double chi) { return exp(-(8.0 / 3.0) 
 // W~_pair(chi) = chi h(chi) exp(-8/(3 chi)) (Eq. wtilde_pair); zero below chi_min, which is
 // 0.01, the lower end of the fitted domain (Sec. 4.2), or larger for the "fast" rate that
 // neglects pair creation below e.g. chi = 0.3 (Sec. 4.2).
-template <typename T>
+template <typename T, bool CH = false>
 __device__ __forceinline__ T wtilde_pair(const T *c, T chi, bool &oor, T chi_min = (T)0.01) {
     using Q = L<T>;
     if (!(chi >= chi_min)) return (T)0;
     T x;
     constexpr int ST = RateSmem<T>::NBW_STRIDE;
     const int p = octave_piece<T, Q::NBW_ELO, Q::NBW_EHI, Q::NBW_SUB, Q::NBW_LOW, Q::NBW_SUBLOW>(chi, x, oor);
-    const T h = horner_smem<Q::NBW_DEG, ST>(c + p * ST, x);
+    const T h = CH ? clenshaw_smem<Q::NBW_DEG, ST>(c + p * ST, x) : horner_smem<Q::NBW_DEG, ST>(c + p * ST, x);
     return chi * h * exp_m83(chi);
 }
 
 // s = 3 chi w^3 / 2 for w-bar = G~_pe(r, chi) (Eq. again, Eq. subs_altri).  TR > 0 reads the
 // table truncated by TR degrees in each variable.
-template <typename T, int TR = 0>
+template <typename T, int TR = 0, bool CH = false>
 __device__ __forceinline__ T photon_s(const T *__restrict__ inv, T chi, T r, bool &oor) {
     using Q = L<T>;
     constexpr int DX = Q::PI_DX - TR, DY = Q::PI_DY - TR;
@@ -157,7 +180,7 @@ __device__ __forceinline__ T photon_s(const T *__restrict__ inv, T chi, T r, boo
     const int ic = octave_piece<T, Q::PI_XELO, Q::PI_XEHI, Q::PI_XSUB, Q::PI_XLOW, Q::PI_XSUBLOW>(chi, xc, oor);
     const int ir = prob_piece<T, Q::PI_YE0, Q::PI_YSUB, Q::PI_YSUBLOW, Q::PI_YQLO, Q::PI_YSUBQ>(r, xr, low, oor);
     const T *c = inv + ((size_t)ic * Q::PI_NY + ir) * ((DX + 1) * padded_row(DY + 1, sizeof(T)));
-    T w = horner2<DX, DY>(c, xc, xr);
+    T w = CH ? clenshaw2<DX, DY>(c, xc, xr) : horner2<DX, DY>(c, xc, xr);
     if (low) w *= r;                          // the low-r block holds w-bar / r
     const T chi_eff = chi > (T)4096 ? (T)4096 : chi;
     return (T)1.5 * chi_eff * w * w * w;
@@ -166,7 +189,7 @@ __device__ __forceinline__ T photon_s(const T *__restrict__ inv, T chi, T r, boo
 // Electron and positron shares for r (Eq. again_pp, Eq. return_to_nrg): the table
 // holds y = 1 - v-bar as a function of (chi, |r'|).
 // y = 1 - v-bar at a = |r'| (Eq. again_pp): the table's value.
-template <typename T, int TR = 0>
+template <typename T, int TR = 0, bool CH = false>
 __device__ __forceinline__ T pair_y(const T *__restrict__ inv, T chi, T a, bool &oor) {
     using Q = L<T>;
     constexpr int DX = Q::PP_DX - TR, DY = Q::PP_DY - TR;
@@ -175,13 +198,13 @@ __device__ __forceinline__ T pair_y(const T *__restrict__ inv, T chi, T a, bool 
     const int ic = octave_piece<T, Q::PP_XELO, Q::PP_XEHI, Q::PP_XSUB, Q::PP_XLOW, Q::PP_XSUBLOW>(chi, xc, oor);
     const int ir = prob_piece<T, Q::PP_YE0, Q::PP_YSUB, Q::PP_YSUBLOW, Q::PP_YQLO, Q::PP_YSUBQ>(a, xr, low, oor);
     const T *c = inv + ((size_t)ic * Q::PP_NY + ir) * ((DX + 1) * padded_row(DY + 1, sizeof(T)));
-    return horner2<DX, DY>(c, xc, xr);
+    return CH ? clenshaw2<DX, DY>(c, xc, xr) : horner2<DX, DY>(c, xc, xr);
 }
 
-template <typename T, int TR = 0>
+template <typename T, int TR = 0, bool CH = false>
 __device__ __forceinline__ void pair_shares(const T *__restrict__ inv, T chi, T r, T &xe, T &xp, bool &oor) {
     const T rp = (T)2 * r - (T)1;
-    const T y = pair_y<T, TR>(inv, chi, fabs(rp), oor);
+    const T y = pair_y<T, TR, CH>(inv, chi, fabs(rp), oor);
     const T small = (T)0.5 * y, big = (T)1 - small;
     if (rp >= (T)0) { xe = big; xp = small; }
     else { xe = small; xp = big; }
@@ -293,7 +316,8 @@ __device__ __forceinline__ void flush_counters(Cnt &c, sfq_counters *out) {
 
 // ---------------------------------------------------------------------------
 // Batched rate kernels (App. A functions 5, 6).
-template <typename T, bool PAIR>
+// CH: the tables hold Chebyshev pieces, evaluated by Clenshaw's recurrence.
+template <typename T, bool PAIR, bool CH = false>
 __global__ void __launch_bounds__(256) rate_kernel(int64_t n, const T *__restrict__ gamma,
                                                    const T *__restrict__ chi, T *__restrict__ rate,
                                                    const T *__restrict__ table, T pref,
@@ -318,9 +342,9 @@ __global__ void __launch_bounds__(256) rate_kernel(int64_t n, const T *__restric
             ++c.v[C_NAN];
             r = (T)0;
         } else if (PAIR) {
-            r = pref * wtilde_pair<T>(tab, x, oor, pair_chi_min) / g;
+            r = pref * wtilde_pair<T, CH>(tab, x, oor, pair_chi_min) / g;
         } else {
-            r = pref * (x / g) * wtilde_rad<T>(tab, x, oor);
+            r = pref * (x / g) * wtilde_rad<T, CH>(tab, x, oor);
         }
         c.v[C_OOR] += oor;
         rate[i] = r;
@@ -329,7 +353,8 @@ __global__ void __launch_bounds__(256) rate_kernel(int64_t n, const T *__restric
 }
 
 // Batched samplers (App. A functions 9 and 11, Eqs. again, again_pp).
-template <typename T, bool PAIR, bool TRUNC>
+// CH: tab.nlc_inv / tab.nbw_inv hold Chebyshev pieces, evaluated by Clenshaw's recurrence.
+template <typename T, bool PAIR, bool TRUNC, bool CH = false>
 __global__ void __launch_bounds__(256) sample_kernel(int64_t n, const T *__restrict__ chi,
                                                      const T *__restrict__ r, T *__restrict__ out_a,
                                                      T *__restrict__ out_b, const Tables<T> tab,
@@ -347,11 +372,12 @@ __global__ void __launch_bounds__(256) sample_kernel(int64_t n, const T *__restr
         }
         if (PAIR) {
             T xe, xp;
-            pair_shares_sel<T, TRUNC>(tab, x, u, xe, xp, oor);
+            if (CH) pair_shares<T, 0, true>(tab.nbw_inv, x, u, xe, xp, oor);
+            else pair_shares_sel<T, TRUNC>(tab, x, u, xe, xp, oor);
             out_a[i] = xe;
             if (out_b) out_b[i] = xp;
         } else {
-            const T s = photon_s_sel<T, TRUNC>(tab, x, u, oor);
+            const T s = CH ? photon_s<T, 0, true>(tab.nlc_inv, x, u, oor) : photon_s_sel<T, TRUNC>(tab, x, u, oor);
             const T inv1s = (T)1 / ((T)1 + s);
             out_a[i] = s * inv1s;          // xi = s/(1+s)
             if (out_b) out_b[i] = inv1s;   // 1 - xi

@@ -29,12 +29,9 @@ static cudaError_t launch_rate_t(const RateLaunch &L, bool pair) {
     const T *g = static_cast<const T *>(L.gamma), *x = static_cast<const T *>(L.chi);
     T *out = static_cast<T *>(L.rate);
     const T *tab = static_cast<const T *>(L.table);
-    if (pair)
-        rate_kernel<T, true><<<L.grid, 256, 0, L.stream>>>(L.n, g, x, out, tab, (T)L.pref, L.counters,
-                                                             (T)L.pair_chi_min);
-    else
-        rate_kernel<T, false><<<L.grid, 256, 0, L.stream>>>(L.n, g, x, out, tab, (T)L.pref, L.counters,
-                                                              (T)L.pair_chi_min);
+    auto kern = pair ? (L.cheb ? rate_kernel<T, true, true> : rate_kernel<T, true, false>)
+                     : (L.cheb ? rate_kernel<T, false, true> : rate_kernel<T, false, false>);
+    kern<<<L.grid, 256, 0, L.stream>>>(L.n, g, x, out, tab, (T)L.pref, L.counters, (T)L.pair_chi_min);
     return cudaGetLastError();
 }
 
@@ -43,7 +40,17 @@ static cudaError_t launch_sample_t(const SampleLaunch &L, bool pair) {
     if (L.n == 0) return cudaSuccess;
     const T *x = static_cast<const T *>(L.chi), *r = static_cast<const T *>(L.r);
     T *a = static_cast<T *>(L.a), *b = static_cast<T *>(L.b);
-    const Tables<T> tab = tables_of<T>(L.ctx);
+    Tables<T> tab = tables_of<T>(L.ctx);
+    if (L.ctx->eval == SFQ_EVAL_CLENSHAW) {
+        // the comparison evaluator: Chebyshev pieces of the full tables, Clenshaw's recurrence
+        tab.nlc_inv = static_cast<const T *>(L.ctx->d_nlc_inv_ch);
+        tab.nbw_inv = static_cast<const T *>(L.ctx->d_nbw_inv_ch);
+        if (pair)
+            sample_kernel<T, true, false, true><<<L.grid, 256, 0, L.stream>>>(L.n, x, r, a, b, tab, L.counters);
+        else
+            sample_kernel<T, false, false, true><<<L.grid, 256, 0, L.stream>>>(L.n, x, r, a, b, tab, L.counters);
+        return cudaGetLastError();
+    }
     const bool tr = tab.tr > 0;
     if (pair && tr)
         sample_kernel<T, true, true><<<L.grid, 256, 0, L.stream>>>(L.n, x, r, a, b, tab, L.counters);

@@ -63,6 +63,52 @@ void cheb_bases(int n, std::vector<double> &c2m, std::vector<double> &m2c) {
         }
 }
 
+// Every 1-D piece (n monomial coefficients) in the Chebyshev basis, same layout.
+template <typename T>
+std::vector<unsigned char> cheb_pieces_1d(const T *src, size_t count, int n) {
+    std::vector<double> c2m, m2c;
+    cheb_bases(n, c2m, m2c);
+    std::vector<unsigned char> out(count * sizeof(T), 0);
+    T *dst = reinterpret_cast<T *>(out.data());
+    for (size_t p = 0; p < count / (size_t)n; ++p)
+        for (int a = 0; a < n; ++a) {
+            double acc = 0.0;
+            for (int k = 0; k < n; ++k) acc += m2c[k * n + a] * (double)src[p * n + k];
+            dst[p * n + a] = (T)acc;
+        }
+    return out;
+}
+
+// Every 2-D piece (n x n monomial coefficients x^i y^j) in the tensor Chebyshev basis
+// T_a(x) T_b(y), rows padded to 16 bytes as on the device.
+template <typename T>
+std::vector<unsigned char> cheb_pieces_2d(const T *src, size_t count, int n) {
+    const int row = (n * (int)sizeof(T) + 15) / 16 * 16 / (int)sizeof(T);
+    const size_t pieces = count / ((size_t)n * n);
+    std::vector<double> c2m, m2c;
+    cheb_bases(n, c2m, m2c);
+    std::vector<unsigned char> out(pieces * (size_t)n * row * sizeof(T), 0);
+    T *dst = reinterpret_cast<T *>(out.data());
+    std::vector<double> Q((size_t)n * n);
+    for (size_t p = 0; p < pieces; ++p) {
+        const T *P = src + p * (size_t)n * n;
+        for (int a = 0; a < n; ++a)
+            for (int j = 0; j < n; ++j) {
+                double acc = 0.0;
+                for (int i = 0; i < n; ++i) acc += m2c[i * n + a] * (double)P[i * n + j];
+                Q[a * n + j] = acc;
+            }
+        T *D = dst + p * (size_t)n * row;
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b < n; ++b) {
+                double acc = 0.0;
+                for (int j = 0; j < n; ++j) acc += Q[a * n + j] * m2c[j * n + b];
+                D[a * row + b] = (T)acc;
+            }
+    }
+    return out;
+}
+
 template <typename T>
 std::vector<unsigned char> truncate_pieces(const T *src, size_t count, int n, int tr) {
     const int m = n - tr;                                   // kept coefficients per variable
@@ -115,6 +161,23 @@ std::vector<unsigned char> truncated_inv_table(int precision, bool pair, int tr)
                     : truncate_pieces(nlc_inv_f64, sizeof(nlc_inv_f64) / sizeof(double), n, tr);
     return pair ? truncate_pieces(nbw_inv_f32, sizeof(nbw_inv_f32) / sizeof(float), n, tr)
                 : truncate_pieces(nlc_inv_f32, sizeof(nlc_inv_f32) / sizeof(float), n, tr);
+}
+
+std::vector<unsigned char> chebyshev_rate_table(int precision, bool pair) {
+    if (precision == SFQ_FP64)
+        return pair ? cheb_pieces_1d(nbw_rate_f64, sizeof(nbw_rate_f64) / sizeof(double), NBW_RATE_F64_DEG + 1)
+                    : cheb_pieces_1d(nlc_rate_f64, sizeof(nlc_rate_f64) / sizeof(double), NLC_RATE_F64_DEG + 1);
+    return pair ? cheb_pieces_1d(nbw_rate_f32, sizeof(nbw_rate_f32) / sizeof(float), NBW_RATE_F32_DEG + 1)
+                : cheb_pieces_1d(nlc_rate_f32, sizeof(nlc_rate_f32) / sizeof(float), NLC_RATE_F32_DEG + 1);
+}
+
+std::vector<unsigned char> chebyshev_inv_table(int precision, bool pair) {
+    const int n = inv_coefficients(precision);
+    if (precision == SFQ_FP64)
+        return pair ? cheb_pieces_2d(nbw_inv_f64, sizeof(nbw_inv_f64) / sizeof(double), n)
+                    : cheb_pieces_2d(nlc_inv_f64, sizeof(nlc_inv_f64) / sizeof(double), n);
+    return pair ? cheb_pieces_2d(nbw_inv_f32, sizeof(nbw_inv_f32) / sizeof(float), n)
+                : cheb_pieces_2d(nlc_inv_f32, sizeof(nlc_inv_f32) / sizeof(float), n);
 }
 
 }  // namespace sfq

@@ -23,6 +23,7 @@ SFQ_SPECIES_SHIFT, SFQ_TAG_SHIFT = 2, 4
 SFQ_ELECTRON, SFQ_POSITRON, SFQ_PHOTON = 0, 1, 2
 SFQ_LEPTON_LCFA_OD, SFQ_LEPTON_BLCFA_LOCAL, SFQ_LEPTON_BLCFA_PUSHED = 0, 1, 2
 SFQ_FIELDS_SOA, SFQ_FIELDS_PLANE_WAVE = 0, 1
+SFQ_EVAL_HORNER, SFQ_EVAL_CLENSHAW = 0, 1
 STATUS = {0: "SFQ_OK", 1: "SFQ_ERR_ARG", 2: "SFQ_ERR_CUDA", 3: "SFQ_ERR_CAPACITY", 4: "SFQ_ERR_TABLE",
           5: "SFQ_ERR_RANGE", 6: "SFQ_ERR_TIMEOUT"}
 COUNTER_NAMES = ["updates", "events", "emitted", "pairs", "dropped", "spawn_dropped", "out_of_range",
@@ -142,6 +143,8 @@ def lib():
         L.sfq_cascade_compact.argtypes = [vp, C.POINTER(Particles), C.POINTER(Fields), C.POINTER(Particles),
                                           C.POINTER(Fields), vp, C.c_size_t, vp]
         L.sfq_cascade_compact.restype = st
+        L.sfq_set_evaluator.argtypes = [vp, C.c_int32]
+        L.sfq_set_evaluator.restype = st
         L.sfq_set_step_shape.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
         L.sfq_set_step_shape.restype = st
         L.sfq_version.restype = C.c_char_p
@@ -156,7 +159,7 @@ EXPORTED = ["sfq_init", "sfq_finalize", "sfq_last_error", "sfq_constants", "sfq_
             "sfq_mlp_num_params", "sfq_mlp_create", "sfq_mlp_destroy", "sfq_mlp_get_params", "sfq_mlp_set_params",
             "sfq_mlp_loss_grad", "sfq_mlp_train", "sfq_mlp_predict_lnw", "sfq_mlp_plain_targets", "sfq_mlp_calibrate",
             "sfq_mlp_sample_photon_xi", "sfq_mlp_create_pair", "sfq_mlp_sample_pair_xi",
-            "sfq_cascade_run", "sfq_cascade_compact_scratch_bytes", "sfq_cascade_compact",
+            "sfq_cascade_run", "sfq_cascade_compact_scratch_bytes", "sfq_cascade_compact", "sfq_set_evaluator",
             "sfq_version"]
 
 
@@ -322,6 +325,10 @@ class Context:
     def set_sampler_coefficients(self, k: int):
         """Use the leading k x k Chebyshev coefficients of each inverse-CDF piece (k = n, n-1, n-2)."""
         self._check(lib().sfq_set_sampler_coefficients(self._h, int(k)), "sfq_set_sampler_coefficients")
+
+    def set_evaluator(self, kind: int):
+        """SFQ_EVAL_HORNER (default) or SFQ_EVAL_CLENSHAW for the rate and sampler entry points."""
+        self._check(lib().sfq_set_evaluator(self._h, kind), "sfq_set_evaluator")
 
     def sampler_coefficients(self):
         """(n, k): coefficients per variable of the tables and those in use."""

@@ -6,7 +6,9 @@ gamma log-uniform in [1e2, 1e5]; one energy sample per particle from Philox,
 seed 0, step 0), plus edge cases: chi = 0, piece boundaries, the ends of the
 fitted ranges, r at the ends of the uniform grid.
 Tolerances: 1e-5 relative on the binary32 path, 1e-10 on the binary64 path; the
-Philox words are compared bit for bit.
+Philox words are compared bit for bit.  Every test runs with both evaluators of the
+fitted tables: Horner on the monomial pieces and Clenshaw on the same pieces in the
+Chebyshev basis (sfq_set_evaluator).
 """
 import numpy as np
 import pytest
@@ -17,13 +19,16 @@ pytestmark = pytest.mark.gpu
 TOL = {"fp32": 1e-5, "fp64": 1e-10}
 
 
-@pytest.fixture(scope="module", params=["fp32", "fp64"])
+@pytest.fixture(scope="module", params=["fp32", "fp64", "fp32/clenshaw", "fp64/clenshaw"])
 def ctx(request):
     import torch
     from paper_2301_07684_gb300 import build, sfq
     build.build()
-    c = sfq.Context(ref_len_m=W.REF_LEN, dt=W.DT, precision=request.param, seed=0)
-    c.name = request.param
+    precision, _, evaluator = request.param.partition("/")
+    c = sfq.Context(ref_len_m=W.REF_LEN, dt=W.DT, precision=precision, seed=0)
+    if evaluator:
+        c.set_evaluator(sfq.SFQ_EVAL_CLENSHAW)
+    c.name = precision
     yield c
     c.close()
 

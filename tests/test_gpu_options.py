@@ -157,3 +157,50 @@ def test_step_with_truncated_sampler(oracle):
     s = compare_lineages(ids, orc, final, prod, TOL["fp32"], nsteps)
     assert s["records"] > 100 and s["near"] <= 2, s
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_clenshaw_evaluator_agrees_with_horner(precision):
+    """The Chebyshev pieces evaluated by Clenshaw's recurrence give Horner's values on the
+    monomial pieces to rounding (rates and both samplers over their whole domains); the
+    evaluator excludes the truncated samplers; switching back restores Horner bit for bit."""
+    import torch
+    from paper_2301_07684_gb300 import build, sfq
+    build.build()
+    ctx = sfq.Context(ref_len_m=W.REF_LEN, dt=W.DT, precision=precision, seed=0)
+    g = np.random.default_rng(4)
+    n = 1 << 16
+    dev = lambda a: torch.as_tensor(a).to(device=ctx.device, dtype=ctx.dtype)
+    chi = dev(10.0 ** g.uniform(-4, 3.2, n))
+    gam = dev(10.0 ** g.uniform(1, 5, n))
+    r = dev(g.uniform(2.0 ** -24, 1 - 2.0 ** -24, n))
+
+    def evaluate():
+        return [ctx.photon_rate(gam, chi), ctx.pair_rate(gam, chi), *ctx.sample_photon_xi(chi, r),
+                *ctx.sample_pair_xi(chi, r)]
+
+    h = evaluate()
+    ctx.set_evaluator(sfq.SFQ_EVAL_CLENSHAW)
+    c = evaluate()
+    # rounding of the two evaluations (binary32: ~2e-7 each, times 3 through s ~ w-bar^3)
+    tol = 4e-6 if precision == "fp32" else 1e-13
+    for a, b in zip(h, c):
+        a, b = a.double().cpu().numpy(), b.double().cpu().numpy()
+        big = np.abs(a) > (np.finfo(np.float32).tiny * 1e3 if precision == "fp32" else 1e-300)
+        assert big.mean() > 0.5
+        assert (np.abs(b[big] - a[big]) / np.abs(a[big])).max() <= tol
+    assert any(not torch.equal(a, b) for a, b in zip(h, c))           # another evaluation ran
+    with pytest.raises(sfq.SfqError):
+        ctx.set_sampler_coefficients(sfq_k(ctx) - 1)
+    ctx.set_evaluator(sfq.SFQ_EVAL_HORNER)
+    for a, b in zip(h, evaluate()):
+        assert torch.equal(a, b)
+    ctx.set_sampler_coefficients(sfq_k(ctx) - 1)
+    with pytest.raises(sfq.SfqError):
+        ctx.set_evaluator(sfq.SFQ_EVAL_CLENSHAW)
+    ctx.close()
+
+
+def sfq_k(ctx):
+    return ctx.sampler_coefficients()[0]
+
