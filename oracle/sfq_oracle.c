@@ -963,7 +963,9 @@ typedef struct {
     uint8_t flags, species, pad[6];
 } orc_cascade_particle;
 
-/* Full cascade: as orc_mc_run, and every product (the photon of an emission, the two
+/* Full cascade (the step of Sec. 2 with the collinear products of Sec. 3; READING: the
+ * paper hands products back to the host code, here every product is stepped again):
+ * as orc_mc_run, and every product (the photon of an emission, the two
  * leptons of a conversion) is also a particle of the lineage, with its own id
  * (orc_child_id), no optical depth yet and zero BLCFA state, stepped from the step after
  * its creation on, in the field of the lineage's primary, and creating particles in turn.
