@@ -341,6 +341,17 @@ sfq_status sfq_sampler_coefficients(const sfq_ctx *ctx, int32_t *n, int32_t *k);
 enum { SFQ_EVAL_HORNER = 0, SFQ_EVAL_CLENSHAW = 1 };
 sfq_status sfq_set_evaluator(sfq_ctx *ctx, int32_t kind);
 
+/* Host copy of a fitted table, without a device or a context: `which` is one of
+ * SFQ_TABLE_NLC_RATE (W~_rad, Eq. wtilde), SFQ_TABLE_NBW_RATE (h of W~_pair, Eq. wtilde_pair),
+ * SFQ_TABLE_NLC_INV (w-bar of Eq. again), SFQ_TABLE_NBW_INV (1 - v-bar of Eq. again_pp), in
+ * `precision`'s element type; `basis` SFQ_EVAL_HORNER gives the monomial pieces,
+ * SFQ_EVAL_CLENSHAW the same pieces in the Chebyshev basis.  Layout as on the device: rate
+ * tables (deg + 1) coefficients per piece; inverse-CDF tables n x n per piece, each row of
+ * n padded to 16 bytes.  *bytes (in: capacity of `out`; out: the table's size) must not be
+ * NULL; `out` may be NULL to query the size, else SFQ_ERR_CAPACITY when it is too small. */
+enum { SFQ_TABLE_NLC_RATE = 0, SFQ_TABLE_NBW_RATE = 1, SFQ_TABLE_NLC_INV = 2, SFQ_TABLE_NBW_INV = 3 };
+sfq_status sfq_table_pieces(int32_t precision, int32_t which, int32_t basis, void *out, size_t *bytes);
+
 /* Autotuner: times every launch shape of sfq_mc_step (kernel variant, particles per lane
  * or warps per block) on a copy of up to `sample_n` particles of `p` (the caller's state
  * is not modified; the copy lives in temporary device memory for the duration of the

@@ -336,6 +336,25 @@ sfq_status sfq_cascade_run(sfq_ctx *ctx, const sfq_particles *p, const sfq_field
 
 size_t sfq_cascade_compact_scratch_bytes(int64_t capacity) { return sfq::compact_scratch_bytes(capacity); }
 
+sfq_status sfq_table_pieces(int32_t precision, int32_t which, int32_t basis, void *out, size_t *bytes) {
+    if (!bytes || (precision != SFQ_FP32 && precision != SFQ_FP64) || which < SFQ_TABLE_NLC_RATE ||
+        which > SFQ_TABLE_NBW_INV || (basis != SFQ_EVAL_HORNER && basis != SFQ_EVAL_CLENSHAW))
+        return SFQ_ERR_ARG;
+    const bool pair = which == SFQ_TABLE_NBW_RATE || which == SFQ_TABLE_NBW_INV;
+    const bool inv = which >= SFQ_TABLE_NLC_INV;
+    const std::vector<unsigned char> t =
+        basis == SFQ_EVAL_HORNER ? sfq::monomial_table(precision, which)
+                                 : (inv ? sfq::chebyshev_inv_table(precision, pair)
+                                        : sfq::chebyshev_rate_table(precision, pair));
+    const size_t cap = *bytes;
+    *bytes = t.size();
+    if (out) {
+        if (cap < t.size()) return SFQ_ERR_CAPACITY;
+        std::memcpy(out, t.data(), t.size());
+    }
+    return SFQ_OK;
+}
+
 sfq_status sfq_cascade_compact(sfq_ctx *ctx, const sfq_particles *src, const sfq_fields *fsrc,
                                const sfq_particles *dst, const sfq_fields *fdst, void *scratch, size_t scratch_bytes,
                                void *stream) {

@@ -122,6 +122,9 @@ std::vector<unsigned char> truncated_inv_table(int precision, bool pair, int tr)
 // inverse-CDF rows padded to 16 bytes), for the Clenshaw comparison evaluator.
 std::vector<unsigned char> chebyshev_rate_table(int precision, bool pair);
 std::vector<unsigned char> chebyshev_inv_table(int precision, bool pair);
+// The monomial tables as the device holds them (which: 0 NLC rate, 1 NBW rate, 2 NLC
+// inverse CDF, 3 NBW inverse CDF).
+std::vector<unsigned char> monomial_table(int precision, int which);
 int inv_coefficients(int precision);   // n of the context's inverse-CDF tables
 
 }  // namespace sfq

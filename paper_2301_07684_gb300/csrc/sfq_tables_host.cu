@@ -180,4 +180,20 @@ std::vector<unsigned char> chebyshev_inv_table(int precision, bool pair) {
                 : cheb_pieces_2d(nlc_inv_f32, sizeof(nlc_inv_f32) / sizeof(float), n);
 }
 
+std::vector<unsigned char> monomial_table(int precision, int which) {
+    const HostTables t = host_tables(precision);
+    const void *src[4] = {t.nlc_rate, t.nbw_rate, t.nlc_inv, t.nbw_inv};
+    const size_t bytes[4] = {t.nlc_rate_bytes, t.nbw_rate_bytes, t.nlc_inv_bytes, t.nbw_inv_bytes};
+    const unsigned char *b = static_cast<const unsigned char *>(src[which]);
+    if (which < 2) return std::vector<unsigned char>(b, b + bytes[which]);
+    // inverse-CDF pieces: rows padded to 16 bytes, as on the device
+    const size_t esz = precision == SFQ_FP64 ? 8 : 4;
+    const size_t n = (size_t)inv_coefficients(precision), rb = n * esz, pb = (rb + 15) / 16 * 16;
+    const size_t rows = bytes[which] / rb;
+    std::vector<unsigned char> out(rows * pb, 0);
+    for (size_t r = 0; r < rows; ++r) std::memcpy(out.data() + r * pb, b + r * rb, rb);
+    return out;
+}
+
 }  // namespace sfq
+

@@ -145,6 +145,8 @@ def lib():
         L.sfq_cascade_compact.restype = st
         L.sfq_set_evaluator.argtypes = [vp, C.c_int32]
         L.sfq_set_evaluator.restype = st
+        L.sfq_table_pieces.argtypes = [C.c_int32, C.c_int32, C.c_int32, vp, C.POINTER(C.c_size_t)]
+        L.sfq_table_pieces.restype = st
         L.sfq_set_step_shape.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
         L.sfq_set_step_shape.restype = st
         L.sfq_version.restype = C.c_char_p
@@ -160,6 +162,7 @@ EXPORTED = ["sfq_init", "sfq_finalize", "sfq_last_error", "sfq_constants", "sfq_
             "sfq_mlp_loss_grad", "sfq_mlp_train", "sfq_mlp_predict_lnw", "sfq_mlp_plain_targets", "sfq_mlp_calibrate",
             "sfq_mlp_sample_photon_xi", "sfq_mlp_create_pair", "sfq_mlp_sample_pair_xi",
             "sfq_cascade_run", "sfq_cascade_compact_scratch_bytes", "sfq_cascade_compact", "sfq_set_evaluator",
+            "sfq_table_pieces",
             "sfq_version"]
 
 
@@ -465,6 +468,24 @@ def sort_scratch_bytes(n):
 
 def cascade_compact_scratch_bytes(capacity):
     return int(lib().sfq_cascade_compact_scratch_bytes(capacity))
+
+
+SFQ_TABLE_NLC_RATE, SFQ_TABLE_NBW_RATE, SFQ_TABLE_NLC_INV, SFQ_TABLE_NBW_INV = 0, 1, 2, 3
+
+
+def table_pieces(precision, which, basis=SFQ_EVAL_HORNER):
+    """Host copy of a fitted table (sfq_table_pieces) as a flat numpy array."""
+    import numpy as np
+    prec = SFQ_FP64 if precision == "fp64" else SFQ_FP32
+    n = C.c_size_t(0)
+    st = lib().sfq_table_pieces(prec, which, basis, None, C.byref(n))
+    if st != 0:
+        raise SfqError(f"sfq_table_pieces: {STATUS.get(st, st)}")
+    out = np.empty(n.value // (8 if prec == SFQ_FP64 else 4), dtype=np.float64 if prec == SFQ_FP64 else np.float32)
+    st = lib().sfq_table_pieces(prec, which, basis, out.ctypes.data_as(C.c_void_p), C.byref(n))
+    if st != 0:
+        raise SfqError(f"sfq_table_pieces: {STATUS.get(st, st)}")
+    return out
 
 
 # --- buffers -------------------------------------------------------------------
