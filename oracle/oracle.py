@@ -256,13 +256,13 @@ def pair_vbar(a, chi):
 
 
 def pair_shares(r, chi):
-    """Electron and positron energy shares for a uniform r (Eq. return_to_nrg)."""
-    r = _f64(r)
-    rp = 2.0 * r - 1.0
-    v, y = pair_vbar(np.abs(rp), chi)
-    big, small = 1.0 - 0.5 * y, 0.5 * y
-    xe = np.where(rp >= 0.0, big, small)
-    xp = np.where(rp >= 0.0, small, big)
+    """Electron and positron energy shares for a uniform r (Eq. return_to_nrg): the C
+    routine the Monte Carlo step calls (orc_pair_shares), batched."""
+    r, c = np.broadcast_arrays(_f64(r), _f64(chi))
+    r, c = _f64(r), _f64(c)
+    xe = np.empty_like(r)
+    xp = np.empty_like(r)
+    lib().orc_batch_pair_shares(_I64(r.size), _p(r), _p(c), _p(xe), _p(xp))
     return xe, xp
 
 

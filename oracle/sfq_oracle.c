@@ -596,6 +596,10 @@ void orc_batch_pair_vbar(int64_t n, const double *a, const double *chi, double *
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t i = 0; i < n; ++i) orc_pair_vbar(a[i], chi[i], &vbar[i], &ybar[i]);
 }
+void orc_batch_pair_shares(int64_t n, const double *r, const double *chi, double *xi_e, double *xi_p) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < n; ++i) orc_pair_shares(r[i], chi[i], &xi_e[i], &xi_p[i]);
+}
 void orc_batch_itilde_pe(int64_t n, const double *w, const double *chi, double *out) {
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t i = 0; i < n; ++i) out[i] = orc_itilde_pe(w[i], chi[i]);

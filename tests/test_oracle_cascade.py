@@ -27,13 +27,16 @@ def _workload(n, nsteps, seed, a0=150.0, gamma0=1e4):
     return d, p, E
 
 
-@pytest.fixture(scope="module")
-def cascade(oracle):
-    n, nsteps = 48, 60
+def make_cascade(oracle, n=48, nsteps=60):
     d, p, E = _workload(n, nsteps, seed=5)
     r = oracle.mc_cascade(p, d["tau"], np.arange(n, dtype=np.uint64), d["flags"], np.zeros(n, np.uint8), E,
                           rho=W.RHO, dt=W.DT, seed=17, nsteps=nsteps)
     return dict(n=n, nsteps=nsteps, d=d, p=p, E=E, r=r, seed=17)
+
+
+@pytest.fixture(scope="module")
+def cascade(oracle):
+    return make_cascade(oracle)
 
 
 def _energy(p, species):

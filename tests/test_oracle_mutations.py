@@ -1,0 +1,79 @@
+"""The oracle's pins catch plausible mistakes: each case plants one mistake in a copy of
+the oracle's C source (compiled apart, on the CPU; the oracle itself is untouched) and
+runs the pins that must then fail.
+
+A wrong coefficient or Bessel order in Eq. wtilde, a sign in Eq. wtilde_pair or
+Eq. pe_eff_int_2, a sign of p x B in Eq. chi_exact, a Philox multiplier, the shares of
+Eq. return_to_nrg given to the wrong lepton, half the optical-depth decrement of Sec. 2,
+the parent tag left out of a descendant's id, and the photon of an emission given the
+lepton's energy in a cascade: every one fails at least one pin.
+"""
+import importlib.util
+import os
+import shutil
+
+import numpy as np
+import pytest
+
+import test_oracle_cascade as PC
+import test_oracle_mc as PM
+import test_oracle_pins as PP
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ORACLE = os.path.join(ROOT, "oracle")
+
+# (name, original text, planted text, pins that must fail)
+CASES = [
+    ("wtilde coefficient", "(45.0 * x * x + 42.0 * x + 20.0)", "(45.0 * x * x + 24.0 * x + 20.0)",
+     [PP.test_wrad_small_chi_series]),
+    ("wtilde Bessel order", "return f * orc_besselk(2.0 / 3.0, v) * 3.0 * t * t;",
+     "return f * orc_besselk(1.0 / 3.0, v) * 3.0 * t * t;", [PP.test_wrad_at_zero]),
+    ("wtilde_pair sign", "return (9.0 - v * v) / (3.0 * om) * orc_besselk(2.0 / 3.0, eta);",
+     "return (9.0 + v * v) / (3.0 * om) * orc_besselk(2.0 / 3.0, eta);",
+     [PP.test_wpair_small_chi_series, PP.test_wpair_vs_scipy]),
+    ("pe CDF sign", "((1.0 + ops * ops) * k23 - ops * ki13)", "((1.0 + ops * ops) * k23 + ops * ki13)",
+     [lambda O: PP.test_pe_cdf_normalisation(O, 1.0)]),
+    ("chi sign of p x B", "{E[0] + b[1] * B[2] - b[2] * B[1],\n                         E[1] + b[2] * B[0] - b[0] * B[2],",
+     "{E[0] + b[1] * B[2] - b[2] * B[1],\n                         E[1] + b[2] * B[0] + b[0] * B[2],",
+     [PP.test_chi_special_cases, PP.test_chi_covariant_form]),
+    ("Philox multiplier", "(uint64_t)0xD2511F53u * c0", "(uint64_t)0xD2511F55u * c0", [PP.test_philox_known_answers]),
+    ("pair shares swapped", "if (rp >= 0.0) { *xi_e = big; *xi_p = small; }",
+     "if (rp < 0.0) { *xi_e = big; *xi_p = small; }", [lambda O: PP.test_pair_sampler_vs_scipy_cdf(O, 1.0, 0.3)]),
+    ("half the optical-depth decrement", "const double tn = s->tau - R * P->dt;\n    if (fabs(tn) <= P->near_od * s->tau0) note_near(info, n);\n    if (!(tn < 0.0)) { s->tau = tn; return; }\n    info->n_events++;\n    const double su",
+     "const double tn = s->tau - 0.5 * R * P->dt;\n    if (fabs(tn) <= P->near_od * s->tau0) note_near(info, n);\n    if (!(tn < 0.0)) { s->tau = tn; return; }\n    info->n_events++;\n    const double su",
+     [PM.test_soft_photon_counts_are_poisson]),
+    ("child id without the parent tag", "0x100u | ((parent_tag & 3u) << 2) | member", "0x100u | member",
+     [PC.test_child_ids_are_philox_words]),
+    ("emitted photon with the lepton's energy", "collinear(nh, gph, pph);", "collinear(nh, gnew, pph);",
+     [lambda O: PC.test_cascade_conserves_energy(PC.make_cascade(O, n=16, nsteps=40))]),
+]
+
+
+def _mutant(tmp, orig, planted):
+    src = open(os.path.join(ORACLE, "sfq_oracle.c")).read()
+    assert src.count(orig) == 1, orig
+    d = str(tmp)
+    shutil.copy(os.path.join(ORACLE, "oracle.py"), os.path.join(d, "oracle.py"))
+    with open(os.path.join(d, "sfq_oracle.c"), "w") as fh:
+        fh.write(src.replace(orig, planted))
+    spec = importlib.util.spec_from_file_location("oracle_mutant_" + os.path.basename(d), os.path.join(d, "oracle.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    assert mod._SRC == os.path.join(d, "sfq_oracle.c")        # builds and loads the planted copy
+    return mod
+
+
+@pytest.mark.parametrize("name,orig,planted,pins", CASES, ids=[c[0] for c in CASES])
+def test_pins_catch_the_planted_mistake(tmp_path, name, orig, planted, pins):
+    mut = _mutant(tmp_path, orig, planted)
+    for pin in pins:
+        with pytest.raises(AssertionError):
+            pin(mut)
+
+
+def test_unplanted_copy_passes_the_same_pins(tmp_path):
+    mut = _mutant(tmp_path, "(45.0 * x * x + 42.0 * x + 20.0)", "(45.0 * x * x + 42.0 * x + 20.0)")
+    PP.test_wrad_small_chi_series(mut)
+    PP.test_wrad_at_zero(mut)
+    PP.test_philox_known_answers(mut)
+    assert np.isfinite(mut.wtilde_rad([1.0])[0])
