@@ -5,8 +5,11 @@ runs the pins that must then fail.
 A wrong coefficient or Bessel order in Eq. wtilde, a sign in Eq. wtilde_pair or
 Eq. pe_eff_int_2, a sign of p x B in Eq. chi_exact, a Philox multiplier, the shares of
 Eq. return_to_nrg given to the wrong lepton, half the optical-depth decrement of Sec. 2,
-the parent tag left out of a descendant's id, and the photon of an emission given the
-lepton's energy in a cascade: every one fails at least one pin.
+the parent tag left out of a descendant's id, the photon of an emission given the
+lepton's energy or a wrong recoil split in a cascade, the pair-rate domain edge of
+Sec. 4.2, another uniform map, the wrong target in the upper tail of Eq. again, the sign
+of the pusher's second electric half-kick, and the constant of Eq. gammaLCFA: every one
+fails at least one pin.
 """
 import importlib.util
 import os
@@ -18,6 +21,7 @@ import pytest
 import test_oracle_cascade as PC
 import test_oracle_mc as PM
 import test_oracle_pins as PP
+import test_oracle_push as PU
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
@@ -46,6 +50,18 @@ CASES = [
      [PC.test_child_ids_are_philox_words]),
     ("emitted photon with the lepton's energy", "collinear(nh, gph, pph);", "collinear(nh, gnew, pph);",
      [lambda O: PC.test_cascade_conserves_energy(PC.make_cascade(O, n=16, nsteps=40))]),
+    ("recoil split", "const double gnew = gamma / (1.0 + su);", "const double gnew = gamma / (1.0 + 2.0 * su);",
+     [lambda O: PC.test_cascade_conserves_energy(PC.make_cascade(O, n=16, nsteps=40))]),
+    ("pair-rate domain edge", "if (chi < 0.01) return 0.0;", "if (chi < 0.001) return 0.0;",
+     [PP.test_pair_rate_cutoff_and_prefactor]),
+    ("uniform map", "((double)(w >> 9) + 0.5) * 0x1p-23", "((double)(w >> 8) + 0.5) * 0x1p-24",
+     [PP.test_uniform_map]),
+    ("photon sampler upper-tail target", "rctx c = {chi, (1.0 - r) * W};", "rctx c = {chi, r * W};",
+     [lambda O: PP.test_photon_sampler_vs_scipy_cdf(O, 1.0, 0.97)]),
+    ("Boris second half-kick sign", "for (int k = 0; k < 3; ++k) u[k] = up[k] + 0.5 * q * dt * E[k];",
+     "for (int k = 0; k < 3; ++k) u[k] = up[k] - 0.5 * q * dt * E[k];", [PU.test_electric_kick]),
+    ("BLCFA threshold constant", "return 0.7 * gamma /", "return 0.75 * gamma /",
+     [PP.test_blcfa_threshold_triple_angle]),
 ]
 
 
