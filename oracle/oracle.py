@@ -241,9 +241,13 @@ def photon_wbar(r, chi):
 
 
 def photon_s(r, chi):
-    """u = 3 chi w-bar^3 / 2; the photon takes xi = s/(1+s) of the lepton energy."""
-    w = photon_wbar(r, chi)
-    return 1.5 * np.broadcast_to(_f64(chi), w.shape) * w ** 3
+    """u = 3 chi w-bar^3 / 2 (Eq. subs_altri); the photon takes xi = s/(1+s) of the lepton
+    energy.  The C routine the Monte Carlo step calls (orc_photon_s), batched."""
+    r, c = np.broadcast_arrays(_f64(r), _f64(chi))
+    r, c = _f64(r), _f64(c)
+    out = np.empty_like(r)
+    lib().orc_batch_photon_s(_I64(r.size), _p(r), _p(c), _p(out))
+    return out
 
 
 def pair_vbar(a, chi):

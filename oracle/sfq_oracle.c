@@ -588,6 +588,10 @@ void orc_batch_pair_rate(int64_t n, const double *gamma, const double *chi, doub
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t i = 0; i < n; ++i) out[i] = orc_pair_rate(gamma[i], chi[i], pref);
 }
+void orc_batch_photon_s(int64_t n, const double *r, const double *chi, double *out) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < n; ++i) out[i] = orc_photon_s(r[i], chi[i]);
+}
 void orc_batch_photon_wbar(int64_t n, const double *r, const double *chi, double *out) {
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t i = 0; i < n; ++i) out[i] = orc_photon_wbar(r[i], chi[i]);

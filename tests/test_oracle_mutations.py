@@ -8,8 +8,9 @@ Eq. return_to_nrg given to the wrong lepton, half the optical-depth decrement of
 the parent tag left out of a descendant's id, the photon of an emission given the
 lepton's energy or a wrong recoil split in a cascade, the pair-rate domain edge of
 Sec. 4.2, another uniform map, the wrong target in the upper tail of Eq. again, the sign
-of the pusher's second electric half-kick, and the constant of Eq. gammaLCFA: every one
-fails at least one pin.
+of the pusher's second electric half-kick, the constant of Eq. gammaLCFA, the sign of
+the projection of Eq. fl_perp, the second difference of Eq. condit, and s of
+Eq. subs_altri: every one fails at least one pin.
 """
 import importlib.util
 import os
@@ -62,6 +63,12 @@ CASES = [
      "for (int k = 0; k < 3; ++k) u[k] = up[k] - 0.5 * q * dt * E[k];", [PU.test_electric_kick]),
     ("BLCFA threshold constant", "return 0.7 * gamma /", "return 0.75 * gamma /",
      [PP.test_blcfa_threshold_triple_angle]),
+    ("sign of the projection in Eq. fl_perp", "for (int k = 0; k < 3; ++k) F[k] = FL[k] - fp * pL[k];",
+     "for (int k = 0; k < 3; ++k) F[k] = FL[k] + fp * pL[k];", [PP.test_blcfa_perpendicular_force_projection]),
+    ("second difference in Eq. condit", "Fdd[k] = (d1[k] - dF[k]) / (dt * dt);", "Fdd[k] = (d1[k] + dF[k]) / (dt * dt);",
+     [PM.test_blcfa_delta_of_a_plane_wave]),
+    ("s of Eq. subs_altri", "return 1.5 * chi * w * w * w;", "return 1.0 * chi * w * w * w;",
+     [lambda O: PP.test_photon_sampler_vs_scipy_cdf(O, 1.0, 0.3)]),
 ]
 
 

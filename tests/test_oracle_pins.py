@@ -327,6 +327,22 @@ def test_chi_covariant_form(oracle):
 
 
 # --- beyond-LCFA ---------------------------------------------------------------
+def test_blcfa_perpendicular_force_projection(oracle):
+    # Eq. fl_perp removes the component of F_L along p_L up to the factor 1/gamma^2 of its
+    # ultrarelativistic form: with p along x, F_L = E = (e_x, e_y, 0) (no B), the component
+    # along p becomes e_x (1 - P^2/gamma^2) = e_x/gamma^2, the transverse one stays e_y,
+    # and Eq. chi_p gives tau_C gamma |F_perp|
+    rho = 1e3
+    for P, ex, ey in [(50.0, 3.0, 0.5), (2.0, -1.5, 4.0), (300.0, 7.0, 0.0)]:
+        g = math.sqrt(1 + P * P)
+        gate, ev, _, _, _ = oracle.blcfa_update((P, 0, 0), (ex, ey, 0), (0, 0, 0), 1e-3, rho, [0.0] * 3, [0.0] * 3,
+                                                True)
+        assert ev.F[0] == pytest.approx(ex / (g * g), rel=1e-10)
+        assert ev.F[1] == pytest.approx(ey, rel=1e-14) and ev.F[2] == 0.0
+        assert ev.gamma == pytest.approx(g, rel=1e-15)
+        assert ev.chi == pytest.approx(g / rho * math.hypot(ex / (g * g), ey), rel=1e-10)
+
+
 def test_blcfa_threshold_triple_angle(oracle):
     # sinh(3 asinh z) = 3 z + 4 z^3, so Eq. gammaLCFA has the closed form below
     for F, delta, g, chi in [((0, 5.0, 0), 1e-9, 2000.0, 0.5), ((1.0, 2.0, 0.5), 3e-7, 500.0, 3.0)]:
@@ -364,6 +380,9 @@ def test_uniform_map(oracle):
         u = oracle.uniform(w)
         assert float(np.float32(u)) == u and float(np.float32(1 - u)) == 1 - u
         assert 2 * u - 1 != 0.0
+    # the vectorised map the tests use is the C map
+    words = np.random.default_rng(3).integers(0, 1 << 32, 2000, dtype=np.uint64).astype(np.uint32)
+    np.testing.assert_array_equal(oracle.uniforms_from_words(words), [oracle.uniform(int(w)) for w in words])
 
 
 def test_philox_uniformity(oracle):
