@@ -9,8 +9,9 @@ the parent tag left out of a descendant's id, the photon of an emission given th
 lepton's energy or a wrong recoil split in a cascade, the pair-rate domain edge of
 Sec. 4.2, another uniform map, the wrong target in the upper tail of Eq. again, the sign
 of the pusher's second electric half-kick, the constant of Eq. gammaLCFA, the sign of
-the projection of Eq. fl_perp, the second difference of Eq. condit, and s of
-Eq. subs_altri: every one fails at least one pin.
+the projection of Eq. fl_perp, the second difference of Eq. condit, s of Eq. subs_altri,
+and a created particle stepped in the step that created it: every one fails at least one
+pin, and every pin passes on an unplanted copy.
 """
 import importlib.util
 import os
@@ -69,6 +70,9 @@ CASES = [
      [PM.test_blcfa_delta_of_a_plane_wave]),
     ("s of Eq. subs_altri", "return 1.5 * chi * w * w * w;", "return 1.0 * chi * w * w * w;",
      [lambda O: PP.test_photon_sampler_vs_scipy_cdf(O, 1.0, 0.3)]),
+    ("created particle stepped in its own step", "for (int c = 0; c < nk; ++c) {\n                orc_state t",
+     "for (int c = 0; c < kids.n; ++c) {\n                orc_state t",
+     [lambda O: PC.test_created_particles_evolve_as_primaries_of_their_own(PC.make_cascade(O), O)]),
 ]
 
 
@@ -94,9 +98,11 @@ def test_pins_catch_the_planted_mistake(tmp_path, name, orig, planted, pins):
             pin(mut)
 
 
-def test_unplanted_copy_passes_the_same_pins(tmp_path):
+def test_unplanted_copy_passes_every_pin(tmp_path):
+    """Control: every pin of every case passes on a copy compiled the same way without a
+    planted mistake, so each case above fails for its mistake and nothing else."""
     mut = _mutant(tmp_path, "(45.0 * x * x + 42.0 * x + 20.0)", "(45.0 * x * x + 42.0 * x + 20.0)")
-    PP.test_wrad_small_chi_series(mut)
-    PP.test_wrad_at_zero(mut)
-    PP.test_philox_known_answers(mut)
+    for name, _, _, pins in CASES:
+        for pin in pins:
+            pin(mut)
     assert np.isfinite(mut.wtilde_rad([1.0])[0])
