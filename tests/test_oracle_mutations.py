@@ -77,7 +77,8 @@ CASES = [
 
 
 def _mutant(tmp, orig, planted):
-    src = open(os.path.join(ORACLE, "sfq_oracle.c")).read()
+    with open(os.path.join(ORACLE, "sfq_oracle.c")) as fh:
+        src = fh.read()
     assert src.count(orig) == 1, orig
     d = str(tmp)
     shutil.copy(os.path.join(ORACLE, "oracle.py"), os.path.join(d, "oracle.py"))
@@ -90,6 +91,8 @@ def _mutant(tmp, orig, planted):
     return mod
 
 
+# a planted mistake may leave scipy's reference quadrature in a pin without convergence
+@pytest.mark.filterwarnings("ignore::scipy.integrate.IntegrationWarning")
 @pytest.mark.parametrize("name,orig,planted,pins", CASES, ids=[c[0] for c in CASES])
 def test_pins_catch_the_planted_mistake(tmp_path, name, orig, planted, pins):
     mut = _mutant(tmp_path, orig, planted)
