@@ -37,7 +37,9 @@ class CascadeRun:
     d: a workload dict with px, py, pz, tau, flags, k0 (uint32 phase index), optionally
     amp (per-particle amplitude) or amp0, table and k_step; ids default to 0 ... n-1 and
     must stay below 2^63.  `capacity` is the initial capacity (at least 3 n), and
-    `products_cap` bounds the product records."""
+    `products_cap` bounds the product records.  Leptons follow the optical-depth model
+    (the buffers carry no beyond-LCFA state; sfq_cascade_run itself accepts populations
+    that do)."""
 
     def __init__(self, ctx: "sfq.Context", d, capacity, products_cap, ids=None):
         dev = ctx.device
