@@ -24,6 +24,7 @@ import test_oracle_cascade as PC
 import test_oracle_mc as PM
 import test_oracle_pins as PP
 import test_oracle_push as PU
+import test_surrogate_oracle as PS
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
@@ -109,3 +110,43 @@ def test_unplanted_copy_passes_every_pin(tmp_path):
         for pin in pins:
             pin(mut)
     assert np.isfinite(mut.wtilde_rad([1.0])[0])
+
+
+# The surrogate's oracle (oracle/surrogate.py, numpy): the same test on a planted copy.
+SURROGATE_CASES = [
+    ("SiLU derivative", "return s * (1.0 + z * (1.0 - s))", "return s * (1.0 + z * s)",
+     [PS.test_gradient_matches_finite_differences]),
+    ("bfloat16 ties", "b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000", "b = (b + 0x8000) & 0xFFFF0000",
+     [PS.test_bf16_rounding_matches_torch]),
+    ("backpropagation through a layer", "d = d @ Wq", "d = d @ Wq * 0.5", [PS.test_gradient_matches_finite_differences]),
+]
+
+
+def _surrogate_mutant(tmp, orig, planted):
+    with open(os.path.join(ORACLE, "surrogate.py")) as fh:
+        src = fh.read()
+    assert src.count(orig) == 1, orig
+    path = os.path.join(str(tmp), "surrogate_planted.py")
+    with open(path, "w") as fh:
+        fh.write(src.replace(orig, planted))
+    spec = importlib.util.spec_from_file_location("oracle.surrogate_planted_" + os.path.basename(str(tmp)), path)
+    mod = importlib.util.module_from_spec(spec)
+    mod.__package__ = "oracle"                                 # its relative import finds the oracle
+    spec.loader.exec_module(mod)
+    return mod
+
+
+@pytest.mark.parametrize("name,orig,planted,pins", SURROGATE_CASES, ids=[c[0] for c in SURROGATE_CASES])
+def test_surrogate_pins_catch_the_planted_mistake(tmp_path, name, orig, planted, pins):
+    mut = _surrogate_mutant(tmp_path, orig, planted)
+    for pin in pins:
+        with pytest.raises(AssertionError):
+            pin(mut)
+
+
+def test_unplanted_surrogate_copy_passes_every_pin(tmp_path):
+    mut = _surrogate_mutant(tmp_path, "d = d @ Wq", "d = d @ Wq")
+    for name, _, _, pins in SURROGATE_CASES:
+        for pin in pins:
+            pin(mut)
+
