@@ -1,5 +1,6 @@
 """The C-ABI library builds for sm_103a, loads, and exports every entry point that
-include/sfq.h declares (no GPU needed: nothing is called)."""
+include/sfq.h declares, and the ctypes binding declares each with the header's number of
+parameters (no GPU needed: nothing is called)."""
 import ctypes
 import os
 import re
@@ -51,3 +52,32 @@ def test_init_rejects_bad_config_without_touching_a_gpu(libsfq):
     cfg = sfq.Config(ref_len_m=1e-7, ref_omega_si=0.0, dt=0.1, precision=7, device=0, seed=0)
     assert L.sfq_init(ctypes.byref(cfg), ctypes.byref(h)) == 1
     assert h.value is None
+
+
+def declared_arity():
+    """Parameter count of every function include/sfq.h declares."""
+    src = open(os.path.join(ROOT, "include", "sfq.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for name, params in re.findall(r"\b(sfq_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S):
+        params = " ".join(params.split())
+        out[name] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_the_header():
+    from paper_2301_07684_gb300 import build, sfq
+    build.build()
+    L = sfq.lib()
+    arity = declared_arity()
+    assert set(arity) == set(sfq.EXPORTED)
+    unbound, wrong = [], []
+    for name, n in sorted(arity.items()):
+        at = getattr(L, name).argtypes
+        if at is None:
+            if n:
+                unbound.append(name)
+        elif len(at) != n:
+            wrong.append((name, len(at), n))
+    assert not wrong, wrong
+    assert not unbound, unbound
