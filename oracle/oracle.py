@@ -366,7 +366,7 @@ def mc_run(p, tau, ids, flags, species, fields, *, rho, dt, seed, step0=0, nstep
     prod = np.zeros(cap_products, dtype=PRODUCT_DTYPE)
     nprod = C.c_int64(0)
     first_near = np.empty(n, dtype=np.int32)
-    n_events = np.empty(n, dtype=np.int32)
+    stats = np.empty((n, 4), dtype=np.int32)
     P = RunParams(rho=rho, pref=rate_prefactor(rho), dt=dt, seed=seed, step0=step0, nsteps=nsteps,
                   lepton_mode=lepton_mode, step_children=int(step_children), near_od=near_od,
                   near_local=near_local, near_blcfa=near_blcfa)
@@ -375,12 +375,19 @@ def mc_run(p, tau, ids, flags, species, fields, *, rho, dt, seed, step0=0, nstep
     f.argtypes = [_I64] + [C.c_void_p] * 9 + [C.POINTER(RunParams), C.c_void_p, _I64,
                                                C.POINTER(C.c_int64), C.c_void_p, C.c_void_p]
     f(_I64(n), _p(p), _p(tau), _p(ids), tagp, _p(flags), _p(species), fp, dfp, _p(fields),
-      C.byref(P), _p(prod), _I64(cap_products), C.byref(nprod), _p(first_near), _p(n_events))
+      C.byref(P), _p(prod), _I64(cap_products), C.byref(nprod), _p(first_near), _p(stats))
     k = nprod.value
     if k > cap_products:
         raise RuntimeError(f"oracle product capacity {cap_products} < {k}")
     return dict(p=p, tau=tau, flags=flags, fprev=fprev, dfprev=dfprev, products=prod[:k].copy(),
-                first_near_step=first_near, n_events=n_events)
+                first_near_step=first_near, **_lineage_stats(stats))
+
+
+def _lineage_stats(stats):
+    """Per-lineage counts: events, beyond-LCFA events whose gate held, events stopped by the
+    0.75 gamma_e rule, samples rejected by Eq. rej_cond."""
+    return dict(n_events=stats[:, 0].copy(), n_gated=stats[:, 1].copy(), n_no_emission=stats[:, 2].copy(),
+                n_rejected=stats[:, 3].copy())
 
 
 def child_id(seed, parent, parent_tag, step, member):
@@ -419,7 +426,7 @@ def mc_cascade(p, tau, ids, flags, species, fields, *, rho, dt, seed, step0=0, n
         out = np.zeros(co, dtype=CASCADE_DTYPE)
         nprod, nout = C.c_int64(0), C.c_int64(0)
         first_near = np.empty(n, dtype=np.int32)
-        n_events = np.empty(n, dtype=np.int32)
+        stats = np.empty((n, 4), dtype=np.int32)
         P = RunParams(rho=rho, pref=rate_prefactor(rho), dt=dt, seed=seed, step0=step0, nsteps=nsteps,
                       lepton_mode=lepton_mode, step_children=1, near_od=near_od, near_local=near_local,
                       near_blcfa=near_blcfa, cascade=1, reserved=0)
@@ -433,12 +440,12 @@ def mc_cascade(p, tau, ids, flags, species, fields, *, rho, dt, seed, step0=0, n
         rc = f(_I64(n), _p(p1), _p(tau1), _p(ids), _p(fl1), _p(species),
                _p(fp1) if fp1 is not None else None, _p(dfp1) if dfp1 is not None else None, _p(fields),
                C.byref(P), _p(prod), _I64(cp), C.byref(nprod), _p(out), _I64(co), C.byref(nout),
-               _p(first_near), _p(n_events))
+               _p(first_near), _p(stats))
         if rc != 0:
             raise RuntimeError("orc_mc_cascade failed")
         if nprod.value <= cp and nout.value <= co:
             break
         cap_products, cap_out = 2 * max(cp, nprod.value), 2 * max(co, nout.value)
     return dict(p=p1, tau=tau1, flags=fl1, fprev=fp1, dfprev=dfp1, products=prod[:nprod.value].copy(),
-                particles=out[:nout.value].copy(), first_near_step=first_near, n_events=n_events)
+                particles=out[:nout.value].copy(), first_near_step=first_near, **_lineage_stats(stats))
 

@@ -708,10 +708,14 @@ typedef struct {
     int64_t *counter;           /* shared product counter (atomic) */
 } orc_prod_sink;
 
-/* Events, near-threshold information and overflow, per primary. */
+/* Events, near-threshold information and overflow, per primary.  The last three count the
+ * beyond-LCFA branches of Sec. 5 taken in the lineage: local events whose gate held (the
+ * threshold of Eq. gammaLCFA applied), events stopped by the 0.75 gamma_e rule, and samples
+ * rejected by Eq. rej_cond. */
 typedef struct {
     int32_t first_near_step;    /* first step with a near-threshold decision in the lineage, or -1 */
     int32_t n_events;
+    int32_t n_gated, n_no_emission, n_rejected;
 } orc_lineage_info;
 
 typedef struct {
@@ -890,14 +894,15 @@ static void step_lepton_blcfa(orc_state *s, const double E[3], const double B[3]
     const double su = orc_photon_s(u[1], ev.chi);
     const double gbar = g * su / (1.0 + su);
     if (gate) {
+        info->n_gated++;
         const double gL = orc_blcfa_threshold(ev.F, ev.delta, g, ev.chi);
         if (fabs(gL - 0.75 * g) <= P->near_blcfa * 0.75 * g) note_near(info, n);
-        if (!(gL < 0.75 * g)) return;                           /* no emission, Sec. 5 */
+        if (!(gL < 0.75 * g)) { info->n_no_emission++; return; }   /* no emission, Sec. 5 */
         if (fabs(gbar - gL) <= P->near_blcfa * gL) note_near(info, n);
         if (!(gbar > gL)) {
             const double Sb = rej_spectrum(gbar, g, ev.chi), SL = rej_spectrum(gL, g, ev.chi);
             if (fabs(u[2] * Sb - SL) <= P->near_blcfa * SL) note_near(info, n);
-            if (!(u[2] * Sb <= SL)) return;                     /* rejected, Eq. rej_cond */
+            if (!(u[2] * Sb <= SL)) { info->n_rejected++; return; }  /* rejected, Eq. rej_cond */
         }
     }
     /* READING: without the gate the field is locally constant (or chi is
@@ -923,11 +928,12 @@ static void step_particle(orc_state *s, const double *EB, uint32_t n, const orc_
  *   fields[n * nsteps * 6]: (Ex,Ey,Ez,Bx,By,Bz) seen by primary i at step j,
  *     index (i*nsteps + j)*6; children created by a primary see its fields.
  * Updates the primaries' state in place, writes products (atomic counter),
- * and per-primary lineage info.  Returns 0. */
+ * and per-primary lineage info: first_near_step[n] and stats[4n] = (events, gated
+ * beyond-LCFA events, events stopped by the 0.75 gamma_e rule, rejected samples).  Returns 0. */
 int orc_mc_run(int64_t n, double *p, double *tau, const uint64_t *id, const uint32_t *tag,
                uint8_t *flags, const uint8_t *species, double *fprev, double *dfprev,
                const double *fields, const orc_run_params *P, orc_product *prod, int64_t cap_products,
-               int64_t *n_products, int32_t *first_near_step, int32_t *n_events) {
+               int64_t *n_products, int32_t *first_near_step, int32_t *stats) {
     *n_products = 0;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t i = 0; i < n; ++i) {
@@ -939,7 +945,7 @@ int orc_mc_run(int64_t n, double *p, double *tau, const uint64_t *id, const uint
         s.flags = flags[i]; s.species = species[i];
         if (fprev) for (int k = 0; k < 3; ++k) { s.Fprev[k] = fprev[3 * i + k]; s.dF[k] = dfprev[3 * i + k]; }
         orc_prod_sink sink = {0, cap_products, prod, n_products};
-        orc_lineage_info info = {-1, 0};
+        orc_lineage_info info = {-1, 0, 0, 0, 0};
         orc_kids kids = {NULL, 0, 0};
         for (uint32_t j = 0; j < P->nsteps; ++j) {
             const uint32_t step = P->step0 + j;
@@ -955,7 +961,10 @@ int orc_mc_run(int64_t n, double *p, double *tau, const uint64_t *id, const uint
         tau[i] = s.tau; flags[i] = s.flags;
         if (fprev) for (int k = 0; k < 3; ++k) { fprev[3 * i + k] = s.Fprev[k]; dfprev[3 * i + k] = s.dF[k]; }
         first_near_step[i] = info.first_near_step;
-        n_events[i] = info.n_events;
+        stats[4 * i] = info.n_events;
+        stats[4 * i + 1] = info.n_gated;
+        stats[4 * i + 2] = info.n_no_emission;
+        stats[4 * i + 3] = info.n_rejected;
     }
     return 0;
 }
@@ -985,7 +994,7 @@ int orc_mc_cascade(int64_t n, double *p, double *tau, const uint64_t *id, uint8_
                    double *fprev, double *dfprev, const double *fields, const orc_run_params *P,
                    orc_product *prod, int64_t cap_products, int64_t *n_products,
                    orc_cascade_particle *out, int64_t cap_out, int64_t *n_out,
-                   int32_t *first_near_step, int32_t *n_events) {
+                   int32_t *first_near_step, int32_t *stats) {
     if (!P->cascade) return -1;
     *n_products = 0;
     *n_out = 0;
@@ -999,7 +1008,7 @@ int orc_mc_cascade(int64_t n, double *p, double *tau, const uint64_t *id, uint8_
         s.flags = flags[i]; s.species = species[i];
         if (fprev) for (int k = 0; k < 3; ++k) { s.Fprev[k] = fprev[3 * i + k]; s.dF[k] = dfprev[3 * i + k]; }
         orc_prod_sink sink = {0, cap_products, prod, n_products};
-        orc_lineage_info info = {-1, 0};
+        orc_lineage_info info = {-1, 0, 0, 0, 0};
         orc_kids kids = {NULL, 0, 0};
         for (uint32_t j = 0; j < P->nsteps; ++j) {
             const uint32_t step = P->step0 + j;
@@ -1016,7 +1025,10 @@ int orc_mc_cascade(int64_t n, double *p, double *tau, const uint64_t *id, uint8_
         tau[i] = s.tau; flags[i] = s.flags;
         if (fprev) for (int k = 0; k < 3; ++k) { fprev[3 * i + k] = s.Fprev[k]; dfprev[3 * i + k] = s.dF[k]; }
         first_near_step[i] = info.first_near_step;
-        n_events[i] = info.n_events;
+        stats[4 * i] = info.n_events;
+        stats[4 * i + 1] = info.n_gated;
+        stats[4 * i + 2] = info.n_no_emission;
+        stats[4 * i + 3] = info.n_rejected;
         for (int c = 0; c < kids.n; ++c) {
             int64_t k;
 #pragma omp atomic capture

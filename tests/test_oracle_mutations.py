@@ -20,6 +20,7 @@ import shutil
 import numpy as np
 import pytest
 
+import test_oracle_blcfa as PB
 import test_oracle_cascade as PC
 import test_oracle_mc as PM
 import test_oracle_pins as PP
@@ -71,6 +72,29 @@ CASES = [
      [PM.test_blcfa_delta_of_a_plane_wave]),
     ("s of Eq. subs_altri", "return 1.5 * chi * w * w * w;", "return 1.0 * chi * w * w * w;",
      [lambda O: PP.test_photon_sampler_vs_scipy_cdf(O, 1.0, 0.3)]),
+    ("Eq. pe_dp integral term dropped",
+     "((1.0 + opu * opu) * orc_besselk(2.0 / 3.0, x) - opu * orc_besselk_int(1.0 / 3.0, x));",
+     "((1.0 + opu * opu) * orc_besselk(2.0 / 3.0, x));",
+     [lambda O: PB.test_spectrum_integrates_to_the_rate(O, 2000.0, 1.0), PB.test_spectrum_soft_photon_end]),
+    ("Eq. pe_dp sign of the integral term", "orc_besselk(2.0 / 3.0, x) - opu * orc_besselk_int(1.0 / 3.0, x));",
+     "orc_besselk(2.0 / 3.0, x) + opu * orc_besselk_int(1.0 / 3.0, x));",
+     [lambda O: PB.test_spectrum_integrates_to_the_rate(O, 2000.0, 1.0), PB.test_spectrum_radiated_power_small_chi]),
+    ("Eq. pe_dp without 1/(1 + u)", "return pref / (ge * ge) / opu *", "return pref / (ge * ge) *",
+     [lambda O: PB.test_spectrum_integrates_to_the_rate(O, 2000.0, 1.0)]),
+    ("Eq. rej_cond reversed", "if (!(u[2] * Sb <= SL)) { info->n_rejected++; return; }",
+     "if (!(u[2] * Sb >= SL)) { info->n_rejected++; return; }",
+     [lambda O: PB.test_rejection_law_of_accepted_photons(O, 0.1, n=1000)]),
+    ("rejection applied above the threshold", "if (!(gbar > gL)) {", "if (!(gbar < gL)) {",
+     [lambda O: PB.test_rejection_law_of_accepted_photons(O, 0.1, n=1000)]),
+    ("no-emission rule reversed", "if (!(gL < 0.75 * g)) { info->n_no_emission++; return; }",
+     "if (!(gL > 0.75 * g)) { info->n_no_emission++; return; }",
+     [lambda O: PB.test_threshold_below_the_rule_still_emits(O, n=600)]),
+    ("no-emission constant below 0.7", "if (!(gL < 0.75 * g)) { info->n_no_emission++; return; }",
+     "if (!(gL < 0.6 * g)) { info->n_no_emission++; return; }",
+     [lambda O: PB.test_threshold_below_the_rule_still_emits(O, n=600)]),
+    ("gate with zeta for zeta^2", "delta / (ORC_ZETA * ORC_ZETA) > out->chi", "delta / ORC_ZETA > out->chi",
+     [PB.test_gate_boundary_delta]),
+    ("gate without chi > zeta", "(out->chi > ORC_ZETA);", "(out->chi > 0.0);", [PB.test_gate_boundary_chi]),
     ("created particle stepped in its own step", "for (int c = 0; c < nk; ++c) {\n                orc_state t",
      "for (int c = 0; c < kids.n; ++c) {\n                orc_state t",
      [lambda O: PC.test_created_particles_evolve_as_primaries_of_their_own(PC.make_cascade(O), O)]),
