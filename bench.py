@@ -60,12 +60,17 @@ class ClockSampler:
         self.lines = []
 
     def start(self):
+        """Start sampling; returns once the first sample has arrived (or after 3 s), so that
+        the timed region that follows is covered from its start."""
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "10"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t_end = time.time() + 3.0
+            while not self.lines and time.time() < t_end and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
 
@@ -122,38 +127,62 @@ def field_slabs(torch, d, nslab, dtype, device):
     return slabs
 
 
-def time_mc(sfq, torch, ctx, P, fields_for_step, steps, warmup, out, counters, n, e2e=None):
-    """Run warmup + steps MC steps; CUDA events around each launch on the launching stream."""
+def time_mc(sfq, torch, ctx, P, fields_for_step, steps, warmup, out, counters, n, e2e=None, reset=None,
+            min_repeats=1, min_total_ms=0.0):
+    """W warm-up steps (0..W-1), then timed regions of exactly `steps` steps (W..W+K-1), each
+    bracketed by a barrier and a device synchronisation; CUDA events around each launch and
+    around each region on the launching stream.  With `reset` every region starts from the
+    same state (reset() restores it, outside the timed region), so all regions do the same
+    work; at least `min_repeats` regions, more until `min_total_ms` of timed work.
+    Returns (region_ms list, launch_ms list of every launch of every region)."""
     stream = torch.cuda.current_stream()
     for s in range(warmup):
         ctx.mc_step(P, fields_for_step(s), s, out, counters=counters)
-    out.reset()
-    counters.zero_()
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    if torch.distributed.is_initialized():
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    t0.record(stream)
-    if e2e is not None:
-        e2e.prepare(warmup)
-    for k in range(steps):
-        s = warmup + k
-        F = fields_for_step(s) if e2e is None else e2e.fields(s)
-        if e2e is not None and k + 1 < steps:
-            e2e.prepare(s + 1)                     # next step's copies overlap this step
-        ev[k][0].record(stream)
-        ctx.mc_step(P, F, s, out, counters=counters)
-        ev[k][1].record(stream)
+    regions, launch_ms = [], []
+    n_regions = None
+    while True:
+        if reset is not None:
+            reset()
+        out.reset()
+        counters.zero_()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        if torch.distributed.is_initialized():
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0.record(stream)
         if e2e is not None:
-            _ = counters[:2].cpu()                 # the step's result read back to the host
-    t1.record(stream)
-    torch.cuda.synchronize()
-    total_ms = t0.elapsed_time(t1)
-    launch_ms = [a.elapsed_time(b) for a, b in ev]
-    return total_ms, launch_ms
+            e2e.prepare(warmup)
+        for k in range(steps):
+            s = warmup + k
+            F = fields_for_step(s) if e2e is None else e2e.fields(s)
+            if e2e is not None and k + 1 < steps:
+                e2e.prepare(s + 1)                 # next step's copies overlap this step
+            ev[k][0].record(stream)
+            ctx.mc_step(P, F, s, out, counters=counters)
+            ev[k][1].record(stream)
+            if e2e is not None:
+                e2e.collect(s)                     # the step's records and counters to the host
+        if e2e is not None:
+            e2e.finish()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        regions.append(t0.elapsed_time(t1))
+        launch_ms += [a.elapsed_time(b) for a, b in ev]
+        if reset is None:
+            break
+        if n_regions is None:
+            # how many regions: decided after the first one, the same on every rank
+            want = max(min_repeats, math.ceil(min_total_ms / max(regions[0], 1e-3)))
+            t = torch.tensor([min(want, 2000)], device=P.px.device)
+            if torch.distributed.is_initialized():
+                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            n_regions = int(t.item())
+        if len(regions) >= n_regions:
+            break
+    return regions, launch_ms
 
 
 def run_ours(args):
@@ -179,7 +208,7 @@ def run_ours(args):
     res = {}
     ids = None
 
-    def one_path(precision, fields_kind, steps, warmup, with_e2e, sampler_k=None):
+    def one_path(precision, fields_kind, steps, warmup, with_e2e, sampler_k=None, keep_final=None):
         dtype = torch.float32 if precision == "fp32" else torch.float64
         ctx = sfq.Context(ref_len_m=W.REF_LEN, dt=W.DT, precision=precision, seed=12345, device=local)
         if sampler_k:
@@ -205,25 +234,60 @@ def run_ours(args):
             tuned = (v, sh, None)
         else:
             tuned = ctx.autotune_step(P, fs(0), 0)
+        init = [t.clone() for t in (P.px, P.py, P.pz, P.tau, P.flags)]
+
+        def reset():
+            for dst, src in zip((P.px, P.py, P.pz, P.tau, P.flags), init):
+                dst.copy_(src)
+
         clocks = ClockSampler(local)
         clocks.start()
-        total_ms, launch_ms = time_mc(sfq, torch, ctx, P, fs, steps, warmup, out, cnt, n)
+        regions, launch_ms = time_mc(sfq, torch, ctx, P, fs, steps, warmup, out, cnt, n, reset=reset,
+                                     min_repeats=args.repeats, min_total_ms=args.min_timed_ms)
         clk = clocks.stop()
+        total_ms = statistics.median(regions)
         c = sfq.counters_dict(cnt)
+        final = None
+        if keep_final:
+            # the last region's final state and records, for the oracle's replay of sampled lineages
+            final = {"ids": keep_final, "px": P.px[keep_final].cpu().numpy(), "py": P.py[keep_final].cpu().numpy(),
+                     "pz": P.pz[keep_final].cpu().numpy(), "tau": P.tau[keep_final].cpu().numpy(),
+                     "flags": P.flags[keep_final].cpu().numpy()}
+            k = min(out.n(), out.capacity)
+            sel = torch.as_tensor(keep_final, device=device) + P.id_base
+            m = torch.isin(out.parent_id[:k], sel)
+            final["records"] = dict(px=out.px[:k][m].cpu().numpy(), py=out.py[:k][m].cpu().numpy(),
+                                    pz=out.pz[:k][m].cpu().numpy(),
+                                    parent_id=(out.parent_id[:k][m] - P.id_base).cpu().numpy().view(np.uint64),
+                                    step=out.step[:k][m].cpu().numpy().view(np.uint32),
+                                    meta=out.meta[:k][m].cpu().numpy())
+        del init
         e2e = None
         if with_e2e and fields_kind == "soa":
-            # end to end through the public API: every step copies its six field arrays
-            # from pinned host memory and reads the step's counters back.  The copies run
-            # on three copy streams into one of two device buffers, so the copies of step
-            # s + 1 overlap the kernel of step s.
+            # end to end through the public API: every step copies its six field arrays from
+            # pinned host memory and brings the step's product records and counters back to
+            # pinned host memory.  The field copies run on three copy streams into one of two
+            # device buffers, so the copies of step s + 1 overlap the kernel of step s; the
+            # records of step s go back on a fourth stream while step s + 1 runs.
+            e2e_steps = max(3, min(steps, 20))
             host = [[a.cpu().pin_memory() for a in slabs[s % nslab]] for s in range(min(nslab, 4))]
             dev_f = [[torch.empty_like(a) for a in slabs[0]] for _ in range(2)]
+            P2 = make_state(sfq, torch, d, dtype, device)
+            P2.id_base = rank * n
+            out2 = sfq.ProductBuffers(int(0.09 * n * (warmup + e2e_steps + 1)) + 4096, dtype, device)
+            cnt2 = sfq.counters_tensor(device)
+            hcap = int(0.09 * n * (e2e_steps + 1)) + 4096
+            hrec = [torch.empty(hcap, dtype=t.dtype).pin_memory()
+                    for t in (out2.px, out2.py, out2.pz, out2.parent_id, out2.step, out2.meta)]
+            hcnt = torch.zeros((e2e_steps + warmup + 1, 16), dtype=torch.int64).pin_memory()
 
             class E2E:
                 streams = [torch.cuda.Stream(device=device) for _ in range(3)]
+                back = torch.cuda.Stream(device=device)
 
                 def __init__(self):
-                    self.done = {}
+                    self.done, self.counted, self.pending = {}, {}, None
+                    self.base, self.h2d, self.d2h = 0, 0, 0
 
                 def prepare(self, s):
                     main = torch.cuda.current_stream()
@@ -233,6 +297,7 @@ def run_ours(args):
                         cs.wait_stream(main)          # the buffer's previous step has finished
                         with torch.cuda.stream(cs):
                             dst.copy_(src, non_blocking=True)
+                        self.h2d += src.numel() * src.element_size()
                         e = torch.cuda.Event()
                         e.record(cs)
                         evs.append(e)
@@ -243,17 +308,53 @@ def run_ours(args):
                         torch.cuda.current_stream().wait_event(e)
                     return sfq.FieldSource.soa(*dev_f[s % 2])
 
-            e2e_fields = E2E()
+                def _records(self, s):
+                    # the counters of step s are on the host once its event completes: copy the
+                    # records it appended, [base, count), while the next step runs
+                    self.counted.pop(s).synchronize()
+                    end = min(int(hcnt[s, 0]), out2.capacity)
+                    a, b = self.base, end
+                    with torch.cuda.stream(self.back):
+                        for dst, src in zip(hrec, (out2.px, out2.py, out2.pz, out2.parent_id, out2.step,
+                                                   out2.meta)):
+                            k = min(b, hcap)
+                            if k > a:
+                                dst[a:k].copy_(src[a:k], non_blocking=True)
+                                self.d2h += (k - a) * src.element_size()
+                    self.base = end
 
-            P2 = make_state(sfq, torch, d, dtype, device)
-            out2 = sfq.ProductBuffers(out.capacity, dtype, device)
-            cnt2 = sfq.counters_tensor(device)
-            e2e_steps = max(3, min(steps, 20))
-            tot2, _ = time_mc(sfq, torch, ctx, P2, fs, e2e_steps, warmup, out2, cnt2, n, e2e=e2e_fields)
+                def collect(self, s):
+                    main = torch.cuda.current_stream()
+                    self.back.wait_stream(main)        # step s has written its records and counters
+                    with torch.cuda.stream(self.back):
+                        hcnt[s, :2].copy_(out2.count, non_blocking=True)
+                        hcnt[s, 2:].copy_(cnt2[:14], non_blocking=True)
+                    self.d2h += 16 * 8
+                    e = torch.cuda.Event()
+                    e.record(self.back)
+                    self.counted[s] = e
+                    if self.pending is not None:
+                        self._records(self.pending)
+                    self.pending = s
+
+                def finish(self):
+                    if self.pending is not None:
+                        self._records(self.pending)
+                        self.pending = None
+                    torch.cuda.current_stream().wait_stream(self.back)
+
+            e2e_fields = E2E()
+            # warm-up steps without read-back, then one timed region with it
+            regions2, _ = time_mc(sfq, torch, ctx, P2, fs, e2e_steps, warmup, out2, cnt2, n, e2e=e2e_fields)
+            tot2 = regions2[0]
+            got = int(hcnt[warmup + e2e_steps - 1, 0])
             e2e = {"value": n * e2e_steps / (tot2 * 1e-3), "unit": UNIT,
-                   "h2d_bytes_per_step": int(sum(a.numel() * a.element_size() for a in dev_f[0])),
-                   "d2h_bytes_per_step": 16}
-            del host, dev_f, P2, out2
+                   "h2d_bytes_per_step": int(e2e_fields.h2d // e2e_steps),
+                   "d2h_bytes_per_step": int(e2e_fields.d2h // e2e_steps),
+                   "steps": e2e_steps, "records_returned": got,
+                   "note": "per step: six SoA field arrays host to device; the step's product records "
+                           "(px, py, pz, parent id, step, meta) and the counters device to host"}
+            del host, dev_f, P2, out2, hrec
         # algorithmic bytes per launch: reads p, tau, flags (+ six fields or the phase index);
         # writes tau; per event: p and one product record (p, parent id, step, meta)
         esz = 4 if precision == "fp32" else 8
@@ -266,6 +367,8 @@ def run_ours(args):
         achieved = bytes_per_launch / avg_launch_s / 1e9
         ups = n * steps / (total_ms * 1e-3)
         out_d = dict(value=ups, ms_per_step=total_ms / steps, launch_ms=statistics.mean(launch_ms),
+                     regions=len(regions), region_ms={"median": total_ms, "min": min(regions), "max": max(regions)},
+                     final=final,
                      achieved_gbs=achieved, frac=achieved / hbm_peak, bytes_per_update=bytes_per_launch / n,
                      events_per_update=events_per_step / n, counters=c, clocks=clk, e2e=e2e,
                      steps=steps, shape={"variant": ["auto", "warp-streaming", "tma-staged"][tuned[0]],
@@ -339,6 +442,108 @@ def run_ours(args):
         ctx.close()
         torch.cuda.empty_cache()
         return out_b
+
+    def config3_leg():
+        """Config 3: 2^24 photons converting by nonlinear Breit-Wheeler (optical depth), the
+        pairs appended as records and stepped from the next step on as beyond-LCFA leptons
+        (local method with the gate, threshold and rejection of Sec. 5); `--config3-steps`
+        steps of two launches each (the leptons, then the photons).  Photon and lepton
+        updates are counted apart; the roofline counts the beyond-LCFA state."""
+        d3 = W.config3(n=n, seed=rank)
+        steps3 = args.config3_steps
+        ctx = sfq.Context(ref_len_m=W.REF_LEN, dt=W.DT, precision="fp32", seed=77, device=local)
+        T = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(device)
+        table = T(d3["table"])
+        k0 = T(d3["k0"].view(np.int32))
+        amp = T(d3["amp"])
+        init = [T(d3[k]) for k in ("px", "py", "pz", "tau", "flags")]
+        P = sfq.ParticleBuffers(*[t.clone() for t in init])
+        P.id_base = rank * n
+        Fp = sfq.FieldSource.plane_wave(k0, table, d3["k_step"], amp=amp)
+        cap = 2 * n + 64                                   # each photon converts at most once
+        z = lambda dtype: torch.zeros(cap, dtype=dtype, device=device)
+        spawn_count = torch.zeros(2, dtype=torch.int64, device=device)
+        Lp = sfq.ParticleBuffers(z(torch.float32), z(torch.float32), z(torch.float32), z(torch.float64),
+                                 z(torch.uint8), ids=z(torch.int64), fprev=[z(torch.float32) for _ in range(3)],
+                                 dfprev=[z(torch.float32) for _ in range(3)],
+                                 lepton_model=sfq.SFQ_LEPTON_BLCFA_LOCAL, n_dev=spawn_count)
+        lk0, lamp = z(torch.int32), z(torch.float32)
+        spawn = sfq.SpawnBuffers(Lp, k0=lk0, amp=lamp)
+        spawn.count = spawn_count
+        Fl = sfq.FieldSource.plane_wave(lk0, table, d3["k_step"], amp=lamp)
+        out = sfq.ProductBuffers(3 * n * steps3 // 4 + 4096, torch.float32, device)   # ~34 records per photon
+        cnt_l, cnt_p = sfq.counters_tensor(device), sfq.counters_tensor(device)
+
+        def reset():
+            for dst, src in zip((P.px, P.py, P.pz, P.tau, P.flags), init):
+                dst.copy_(src)
+            spawn_count.zero_()
+            out.reset()
+            cnt_l.zero_()
+            cnt_p.zero_()
+
+        for s in range(min(3, steps3)):                    # warm-up, then the run from the start
+            ctx.mc_step(Lp, Fl, s, out, counters=cnt_l)
+            ctx.mc_step(P, Fp, s, out, spawn=spawn, counters=cnt_p)
+        reset()
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        E = lambda: torch.cuda.Event(enable_timing=True)
+        evl = [(E(), E()) for _ in range(steps3)]
+        evp = [(E(), E()) for _ in range(steps3)]
+        t0, t1 = E(), E()
+        clocks = ClockSampler(local)
+        clocks.start()
+        t0.record(stream)
+        for s in range(steps3):
+            evl[s][0].record(stream)
+            ctx.mc_step(Lp, Fl, s, out, counters=cnt_l)
+            evl[s][1].record(stream)
+            evp[s][0].record(stream)
+            ctx.mc_step(P, Fp, s, out, spawn=spawn, counters=cnt_p)
+            evp[s][1].record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = t0.elapsed_time(t1)
+        ms_l = sum(a.elapsed_time(b) for a, b in evl)
+        ms_p = sum(a.elapsed_time(b) for a, b in evp)
+        cl, cp = sfq.counters_dict(cnt_l), sfq.counters_dict(cnt_p)
+        # algorithmic bytes (binary32 momenta, binary64 optical depth):
+        #   photon update: p 12 + tau 8 + flags 1 + phase index 4 + amplitude 4 read, tau 8 written;
+        #   conversion: flags 1 + two records (2 x 25) + two stepped leptons (2 x 61: p, tau, id,
+        #   flags, force history 24, phase index, amplitude);
+        #   lepton update: p 12 + flags 1 + id 8 + phase index 4 + amplitude 4 + force history 24
+        #   read, force history 24 written; emission: p 12 + one record 25
+        b_p = cp["updates"] * 37 + cp["pairs"] * 173
+        b_l = cl["updates"] * 77 + cl["emitted"] * 37
+        upd = cp["updates"] + cl["updates"]
+        res3 = {"workload": "config3: 2^24 photons, chi_peak log-U[0.1,100], gamma log-U[1e2,1e5], head-on plane "
+                            "wave per photon, NBW by optical depth, pairs stepped as beyond-LCFA leptons (local "
+                            "method, Sec. 5), fp32 with fp64 optical depth",
+                "photons": n, "steps": steps3, "value": upd / (ms * 1e-3), "unit": UNIT, "ms": ms,
+                "ms_per_step": ms / steps3, "photon_updates": cp["updates"], "lepton_updates": cl["updates"],
+                "photon_updates_per_s": cp["updates"] / (ms_p * 1e-3),
+                "lepton_updates_per_s": cl["updates"] / max(ms_l, 1e-9) * 1e3,
+                "pairs": cp["pairs"], "leptons": int(spawn_count[0].item()), "emitted": cl["emitted"],
+                "blcfa_rejected": cl["blcfa_rejected"], "blcfa_no_emission": cl["blcfa_no_emission"],
+                "dropped": cp["dropped"] + cl["dropped"] + cp["spawn_dropped"], "records": out.n(),
+                "roofline": {"bound": "hbm", "unit": "GB/s", "peak": hbm_peak,
+                             "photon_kernel": {"achieved": b_p / (ms_p * 1e-3) / 1e9,
+                                               "frac": b_p / (ms_p * 1e-3) / 1e9 / hbm_peak,
+                                               "bytes_per_update": b_p / max(cp["updates"], 1)},
+                             "lepton_kernel": {"achieved": b_l / max(ms_l, 1e-9) / 1e6,
+                                               "frac": b_l / max(ms_l, 1e-9) / 1e6 / hbm_peak,
+                                               "bytes_per_update": b_l / max(cl["updates"], 1)},
+                             "whole_step": {"achieved": (b_p + b_l) / (ms * 1e-3) / 1e9,
+                                            "frac": (b_p + b_l) / (ms * 1e-3) / 1e9 / hbm_peak}},
+                "clocks": clk}
+        if rank == 0 and world == 1 and args.config3_oracle_photons > 0:
+            res3["cpu_baseline"] = oracle_config3_sample(args.config3_oracle_photons, steps3)
+        del P, Lp, out, init
+        ctx.close()
+        torch.cuda.empty_cache()
+        return res3
 
     def cascade_leg():
         """Full cascade: 2^20 electrons of gamma ~ N(1e4, 5%) head-on with the plane wave of
@@ -589,7 +794,9 @@ def run_ours(args):
 
     legs = set(args.legs.split(","))
     config1 = config1_leg() if "config1" in legs else None
-    main = one_path("fp32", "soa", args.steps, args.warmup, with_e2e=True)
+    replay_ids = (W.sample_ids(n, args.oracle_particles, seed=17).tolist()
+                  if world == 1 and args.oracle_particles > 0 else None)
+    main = one_path("fp32", "soa", args.steps, args.warmup, with_e2e=True, keep_final=replay_ids)
     fused = fused_leg("fp32") if "fused" in legs and args.fused else None
     fused64 = fused_leg("fp64") if "fused64" in legs and args.fused else None
     pw = one_path("fp32", "pw", args.steps, args.warmup, with_e2e=False) if "pw" in legs else None
@@ -598,8 +805,26 @@ def run_ours(args):
     trunc = one_path("fp32", "soa", args.steps, args.warmup, with_e2e=False, sampler_k=8) if "trunc" in legs else None
     batched = batched_leg() if "batched" in legs and args.batched_steps > 0 else None
     casc = cascade_leg() if "cascade" in legs and args.cascade_steps > 0 else None
+    config3 = config3_leg() if "config3" in legs and args.config3_steps > 0 else None
     evaluators = evaluator_leg() if "evaluators" in legs else None
     surrogate = surrogate_leg() if "surrogate" in legs and args.surrogate_steps > 0 else None
+
+    def fp64_entry(f64, sms):
+        """The binary64 path against its own roofline: FP64-pipe instructions per second (the
+        per-update count from the ncu capture times the measured update rate) over the nominal
+        FP64 peak of 1.25 TFLOP/s dense, i.e. 1.25e12 / 2 flops per DFMA / (152 SMs x 2.07 GHz)
+        = 1.99 FP64 instructions per clock per SM, at the SM clock sampled during the region."""
+        mhz = (f64["clocks"] or {}).get("sm_mhz") or 2070.0
+        peak = 1.25e12 / 2 / (152 * 2.07e9) * sms * mhz * 1e6
+        ach = f64["value"] * args.fp64_inst_per_update
+        return {"value": f64["value"], "unit": UNIT, "ms_per_step": f64["ms_per_step"],
+                "achieved_gbs": f64["achieved_gbs"], "hbm_frac": f64["frac"], "steps": f64["steps"],
+                "regions": f64["regions"],
+                "roofline": {"bound": "alu", "unit": "FP64 instructions/s", "achieved": ach, "peak": peak,
+                             "frac": ach / peak, "fp64_inst_per_update": args.fp64_inst_per_update,
+                             "peak_source": "nominal 1.25 TFLOP/s dense FP64 = 1.99 DFMA/clk/SM at the sampled clock",
+                             "pipe_busy_ncu": args.fp64_pipe_busy,
+                             "source": "FP64-pipe instructions per update from the ncu capture of the 2^22 case"}}
 
     # max over ranks of the headline time
     t = torch.tensor([main["ms_per_step"]], device=device)
@@ -609,7 +834,11 @@ def run_ours(args):
     total_updates = n * world
     value = total_updates / (ms * 1e-3)
     if rank == 0:
-        cpu = cpu_baseline(args) if world == 1 else None
+        replay = None
+        if main["final"] is not None:
+            replay = dict(d=d, final=main["final"], warmup=args.warmup, steps=args.steps, seed=12345)
+        cpu = cpu_baseline(args, replay) if world == 1 else None
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
         dev_name = torch.cuda.get_device_name(local)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -630,15 +859,9 @@ def run_ours(args):
             "e2e": main["e2e"],
             "gpu_launches": args.steps,
             "clocks": main["clocks"],
-            "fp64_path": None if f64 is None else {"value": f64["value"], "unit": UNIT, "ms_per_step": f64["ms_per_step"],
-                          "achieved_gbs": f64["achieved_gbs"], "hbm_frac": f64["frac"],
-                          "steps": f64["steps"], "bound": "alu (fp64 pipe)",
-                          "roofline": {"bound": "alu", "unit": "FP64 instructions/s",
-                                       "achieved": f64["value"] * args.fp64_inst_per_update,
-                                       "fp64_inst_per_update": args.fp64_inst_per_update,
-                                       "frac": args.fp64_pipe_busy,
-                                       "source": "ncu of the 2^22 capture: FP64-pipe instructions per update "
-                                                 "and sm__pipe_fp64_cycles_active (the pipe's busy fraction)"}},
+            "regions": {"count": main["regions"], "ms": main["region_ms"]},
+            "parity_sample": (cpu or {}).get("parity_sample"),
+            "fp64_path": None if f64 is None else fp64_entry(f64, sms),
             "plane_wave_fields": None if pw is None else {"value": pw["value"], "unit": UNIT, "ms_per_step": pw["ms_per_step"],
                                   "achieved_gbs": pw["achieved_gbs"], "frac": pw["frac"],
                                   "bytes_per_update": pw["bytes_per_update"]},
@@ -651,6 +874,7 @@ def run_ours(args):
             "fused_plane_wave_fp64": fused64,
             "batched": batched,
             "cascade": casc,
+            "config3": config3,
             "evaluators": evaluators,
             "surrogate": surrogate,
             "events_per_update": main["events_per_update"],
@@ -704,13 +928,91 @@ def oracle_config1(n_sample=1024):
             "full_config_s": sec * d["chi_e"].size / n_sample}
 
 
-def cpu_baseline(args):
-    upd, sec, thr = oracle_sample_run(args.oracle_particles, args.oracle_steps)
+def oracle_config3_sample(n_photons, nsteps):
+    """The oracle on config 3: n_photons photon lineages (the photon, its pair and the pair's
+    photons) over all steps.  Updates are counted from the records: a photon converted at
+    step s made s + 1 updates and each of its leptons nsteps - 1 - s; an unconverted photon
+    made nsteps."""
+    from oracle import oracle as O
+    from paper_2301_07684_gb300 import workloads as W
+    O.build()
+    d = W.config3(n=max(n_photons, 1024), seed=0)
+    ids = np.arange(n_photons)
+    E = np.zeros((n_photons, nsteps, 6))
+    for j in range(nsteps):
+        (_, ey, _), (_, _, bz) = W.plane_wave_fields(d["k0"][ids], d["amp"][ids], d["table"], j)
+        E[:, j, 1], E[:, j, 5] = ey, bz
+    p = np.stack([d["px"][ids], d["py"][ids], d["pz"][ids]], 1).astype(np.float64)
+    t = time.perf_counter()
+    r = O.mc_run(p, d["tau"][ids], ids.astype(np.uint64), d["flags"][ids], (d["flags"][ids] >> 2) & 3, E,
+                 rho=W.RHO, dt=W.DT, seed=77, nsteps=nsteps, lepton_mode=O.MODE_BLCFA_LOCAL, step_children=True,
+                 cap_products=64 * n_photons * nsteps)
+    sec = time.perf_counter() - t
+    conv = r["products"][r["products"]["member"] == 1]["step"].astype(np.int64)
+    upd = int((n_photons - conv.size) * nsteps + (conv + 1).sum() + 2 * (nsteps - 1 - conv).sum())
+    return {"value": upd / sec, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{n_photons} photon lineages x {nsteps} steps of config 3 ({upd} updates in {sec:.1f} s)"}
+
+
+def oracle_replay(rep):
+    """The oracle replays sampled lineages of the timed run: the same particles from the same
+    initial state over the same steps (W .. W+K-1), fields and Philox key.  Returns
+    (updates, seconds, threads, parity), parity comparing the oracle's decisions (the steps
+    at which each lineage emitted) with the records the GPU wrote in its last timed region:
+    lineages whose decisions match, lineages cut at a near-threshold decision (|tau_d| <=
+    1e-6 tau0, counted, compared up to that step), mismatches elsewhere, and the largest
+    relative difference of a record's momentum."""
+    from oracle import oracle as O
+    from paper_2301_07684_gb300 import workloads as W
+    O.build()
+    d, fin, K, s0 = rep["d"], rep["final"], rep["steps"], rep["warmup"]
+    ids = np.asarray(fin["ids"], np.int64)
+    E = np.zeros((ids.size, K, 6))
+    for j in range(K):
+        (_, ey, _), (_, _, bz) = W.plane_wave_fields(d["k0"][ids], d["amp0"], d["table"], s0 + j)
+        E[:, j, 1], E[:, j, 5] = ey, bz
+    p = np.stack([d["px"][ids], d["py"][ids], d["pz"][ids]], 1).astype(np.float64)
+    t = time.perf_counter()
+    orc = O.mc_run(p, d["tau"][ids], ids.astype(np.uint64), d["flags"][ids], np.zeros(ids.size, np.uint8), E,
+                   rho=W.RHO, dt=W.DT, seed=rep["seed"], step0=s0, nsteps=K, near_od=1e-6)
+    sec = time.perf_counter() - t
+    op, gr = orc["products"], fin["records"]
+    near = mism = 0
+    worst = 0.0
+    for j, pid in enumerate(ids.tolist()):
+        cut = orc["first_near_step"][j] if orc["first_near_step"][j] >= 0 else s0 + K
+        near += orc["first_near_step"][j] >= 0
+        mo = np.nonzero((op["parent_id"] == pid) & (op["step"] < cut))[0]
+        mg = np.nonzero((gr["parent_id"] == pid) & (gr["step"] < cut))[0]
+        so, sg = np.sort(op["step"][mo]), np.sort(gr["step"][mg])
+        if not np.array_equal(so, sg):
+            mism += 1
+            continue
+        mo, mg = mo[np.argsort(op["step"][mo])], mg[np.argsort(gr["step"][mg])]
+        for a, b in zip(mo, mg):
+            po = op["p"][a]
+            pg = np.array([gr["px"][b], gr["py"][b], gr["pz"][b]], np.float64)
+            worst = max(worst, float(np.linalg.norm(pg - po) / np.linalg.norm(po)))
+    parity = {"lineages": int(ids.size), "steps": K, "events": int(orc["n_events"].sum()),
+              "near_threshold_lineages": int(near), "decision_mismatches": int(mism),
+              "max_record_rel_diff": worst,
+              "protocol": "decisions compared up to the first near-threshold one (|tau_d| <= 1e-6 tau0)"}
+    return ids.size * K, sec, O.num_threads(), parity
+
+
+def cpu_baseline(args, replay=None):
+    if replay is not None:
+        upd, sec, thr, parity = oracle_replay(replay)
+        sample = (f"{len(replay['final']['ids'])} sampled particles x {replay['steps']} steps of the timed run, "
+                  f"replayed from its initial state ({upd} updates in {sec:.1f} s)")
+    else:
+        upd, sec, thr = oracle_sample_run(args.oracle_particles, args.oracle_steps)
+        parity = None
+        sample = (f"{args.oracle_particles} particles x {args.oracle_steps} steps of the same workload "
+                  f"({upd} updates in {sec:.1f} s)")
     c1 = oracle_config1() if args.oracle_config1 else None
-    return {"value": upd / sec, "unit": UNIT, "cores": thr, "kind": "oracle",
-            "sample": f"{args.oracle_particles} particles x {args.oracle_steps} steps of the same workload "
-                      f"({upd} updates in {sec:.1f} s)",
-            "config1": c1}
+    return {"value": upd / sec, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sample,
+            "parity_sample": parity, "config1": c1}
 
 
 def run_reference(args):
@@ -753,12 +1055,20 @@ def main():
                     help="training steps of the surrogate leg (0 skips it)")
     ap.add_argument("--fused", type=int, default=1, help="time the fused multi-step plane-wave run (0: skip)")
     ap.add_argument("--cascade-steps", type=int, default=100, help="steps of the full-cascade leg")
-    ap.add_argument("--legs", default="config1,pw,fp64,trunc,fused,fused64,batched,cascade,evaluators,surrogate",
+    ap.add_argument("--config3-steps", type=int, default=100, help="steps of the config-3 leg (0 skips it)")
+    ap.add_argument("--config3-oracle-photons", type=int, default=32,
+                    help="photon lineages of config 3 the oracle replays for its CPU baseline")
+    ap.add_argument("--legs", default="config1,pw,fp64,trunc,fused,fused64,batched,cascade,config3,evaluators,surrogate",
                     help="legs timed beside the headline step (comma list; the headline always runs)")
     ap.add_argument("--shape", default="",
                     help="fixed launch shape 'variant:shape' of the per-step legs (e.g. 2:16) instead of the autotuner")
     ap.add_argument("--oracle-config1", type=int, default=1, help="also time the oracle on config 1 (0: skip)")
-    ap.add_argument("--oracle-particles", type=int, default=512)
+    ap.add_argument("--oracle-particles", type=int, default=512,
+                    help="sampled particles of the timed run the oracle replays (CPU baseline and parity sample)")
+    ap.add_argument("--repeats", type=int, default=10,
+                    help="timed regions of --steps steps each (at least); the line reports the median")
+    ap.add_argument("--min-timed-ms", type=float, default=1500.0,
+                    help="add regions until this much timed work (so the clock sampler sees the region)")
     ap.add_argument("--oracle-steps", type=int, default=50)
     # DRAM bytes (read + write) per update of mc_step_tma_kernel<float, SoA, 16 warps>, from the
     # ncu capture summarised in profiles/mc_step_tma_fp32_soa_4M.md (4,194,304 particles;

@@ -35,10 +35,10 @@ typedef enum {
     SFQ_OK = 0,
     SFQ_ERR_ARG = 1,       /* invalid argument: NULL, misaligned, negative size, bad enum */
     SFQ_ERR_CUDA = 2,      /* a CUDA runtime call failed (message in sfq_last_error) */
-    SFQ_ERR_CAPACITY = 3,  /* reported by sfq_counters_check: products were dropped */
-    SFQ_ERR_TABLE = 4,     /* approximation tables missing or inconsistent */
-    SFQ_ERR_RANGE = 5,     /* reported by sfq_counters_check: inputs outside the fitted range */
-    SFQ_ERR_TIMEOUT = 6    /* reserved: a bounded device wait gave up */
+    SFQ_ERR_CAPACITY = 3,  /* reported by sfq_counters_check: product records or children were dropped */
+    SFQ_ERR_TABLE = 4,     /* sfq_init: a fitted table is missing, of inconsistent size, or not finite */
+    SFQ_ERR_RANGE = 5,     /* reported by sfq_counters_check: inputs outside the fitted range, or NaN */
+    SFQ_ERR_TIMEOUT = 6    /* reported by sfq_counters_check: a bounded device wait gave up */
 } sfq_status;
 
 enum { SFQ_FP32 = 0, SFQ_FP64 = 1 };
@@ -211,6 +211,21 @@ typedef struct sfq_counters {
     unsigned long long reserved[2];
 } sfq_counters;
 
+/* Status of a run from a HOST copy of its counters (copy them back after the stream has
+ * synchronised): SFQ_ERR_TIMEOUT if a bounded device wait gave up (the run's results are
+ * then invalid), else SFQ_ERR_CAPACITY if product records or children were dropped, else
+ * SFQ_ERR_RANGE if chi fell outside the fitted range (evaluated clamped) or an input was
+ * NaN, else SFQ_OK.  SFQ_ERR_ARG for NULL.  Reads no device memory and needs no context. */
+sfq_status sfq_counters_check(const sfq_counters *host_counters);
+
+/* Check of the bounded device waits the kernels use (no counterpart in the paper): one CTA
+ * waits, with the step kernel's bounded mbarrier wait, on a barrier that nothing completes,
+ * gives up after `polls` polls, adds 1 to counters->timeouts and returns, so that a host
+ * can see that a wait which gives up is reported and leaves the context usable.
+ * polls in [1, 65536] (else SFQ_ERR_ARG); `counters` a device pointer, not NULL.
+ * Asynchronous on `stream`. */
+sfq_status sfq_check_bounded_wait(sfq_ctx *ctx, uint32_t polls, sfq_counters *counters, void *stream);
+
 /* One Monte Carlo step for every alive particle of `p` (Sec. 2 and 4; Sec. 5 for
  * BLCFA leptons):
  *   chi (Eq. chi_exact) -> rate (Eq. pe_rate_3 / Eq. pp_tot_real) -> leptons with
@@ -380,8 +395,9 @@ sfq_status sfq_sort_products(sfq_ctx *ctx, const sfq_products *out, int64_t n, v
  *   Nothing in the scratch needs to start at zero.
  *   The array is shared by all calls on a device: calls that overlap in time on one
  *   device race, so issue them on one stream or order their streams.
- *   The first call on each device looks up the array's address (cudaGetSymbolAddress);
- *   make that first call before any stream capture begins.
+ *   The first call with each context looks up the array's address on the context's device
+ *   (cudaGetSymbolAddress) and keeps it in the context; make that first call before any
+ *   stream capture begins.
  *   Synchronises `stream` once, as sfq_sort_products does. */
 #define SFQ_SORT_NOALLOC_MAX_N (1 << 20)
 #define SFQ_SORT_NOALLOC_SCRATCH_BYTES (44u << 20)

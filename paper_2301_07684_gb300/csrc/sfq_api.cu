@@ -161,7 +161,24 @@ sfq_status sfq_init(const sfq_config *cfg, sfq_ctx **out) {
     const int row[6] = {0, 0, (f64 ? NLC_INV_F64_DY : NLC_INV_F32_DY) + 1, (f64 ? NBW_INV_F64_DY : NBW_INV_F32_DY) + 1,
                         0, 0};
     for (int k = 0; k < 6; ++k) {
-        if (!src[k] || bytes[k] == 0) { sfq_finalize(ctx); return SFQ_ERR_TABLE; }
+        if (!src[k] || bytes[k] == 0 || bytes[k] % esz) { sfq_finalize(ctx); return SFQ_ERR_TABLE; }
+        // every coefficient of a fitted table is finite
+        for (size_t j = 0; j < bytes[k] / esz; ++j) {
+            const unsigned char *q = static_cast<const unsigned char *>(src[k]) + j * esz;
+            double v;
+            if (f64) {
+                std::memcpy(&v, q, 8);
+            } else {
+                float w;
+                std::memcpy(&w, q, 4);
+                v = w;
+            }
+            if (!std::isfinite(v)) {
+                ctx->err = "fitted table has a non-finite coefficient";
+                sfq_finalize(ctx);
+                return SFQ_ERR_TABLE;
+            }
+        }
         std::vector<unsigned char> padded;
         const void *h = src[k];
         size_t nb = bytes[k];
@@ -492,6 +509,23 @@ sfq_status sfq_set_step_shape(sfq_ctx *ctx, int32_t variant, int32_t ppt, int32_
     ctx->step_ppt = ppt;
     ctx->step_grid = grid_blocks;
     return SFQ_OK;
+}
+
+sfq_status sfq_counters_check(const sfq_counters *c) {
+    if (!c) return SFQ_ERR_ARG;
+    if (c->timeouts) return SFQ_ERR_TIMEOUT;
+    if (c->dropped || c->spawn_dropped) return SFQ_ERR_CAPACITY;
+    if (c->out_of_range || c->nan_input) return SFQ_ERR_RANGE;
+    return SFQ_OK;
+}
+
+sfq_status sfq_check_bounded_wait(sfq_ctx *ctx, uint32_t polls, sfq_counters *counters, void *stream) {
+    if (!ctx) return SFQ_ERR_ARG;
+    if (!counters || !aligned8(counters)) return fail(ctx, SFQ_ERR_ARG, "counters null or misaligned");
+    if (polls < 1 || polls > 65536) return fail(ctx, SFQ_ERR_ARG, "polls must be in [1, 65536]");
+    DeviceGuard g(ctx->device);
+    const cudaError_t e = sfq::launch_wait_check(polls, counters, (cudaStream_t)stream);
+    return e == cudaSuccess ? SFQ_OK : cuda_fail(ctx, e, "bounded-wait check");
 }
 
 }  // extern "C"

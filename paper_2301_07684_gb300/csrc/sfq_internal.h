@@ -26,6 +26,7 @@ struct sfq_ctx {
     int eval = 0;                 // SFQ_EVAL_HORNER or SFQ_EVAL_CLENSHAW (sfq_set_evaluator)
     void *d_nlc_rate_ch = nullptr, *d_nbw_rate_ch = nullptr;   // Chebyshev pieces (Clenshaw evaluator)
     void *d_nlc_inv_ch = nullptr, *d_nbw_inv_ch = nullptr;
+    void *noalloc_scratch = nullptr;   // address of the no-allocation sort's array on this context's device
     std::string err;
 };
 
@@ -101,6 +102,8 @@ cudaError_t launch_cascade_sync(unsigned long long *count, unsigned long long *n
 size_t compact_scratch_bytes(int64_t capacity);
 cudaError_t launch_compact(int precision, const sfq_particles &src, const sfq_fields &fsrc, const sfq_particles &dst,
                            const sfq_fields &fdst, void *scratch, cudaStream_t s);
+// One CTA whose bounded mbarrier wait gives up after `polls` polls (sfq_check_bounded_wait).
+cudaError_t launch_wait_check(uint32_t polls, sfq_counters *c, cudaStream_t s);
 // Dynamic shared-memory attributes of every kernel shape (before graph capture).
 cudaError_t prepare_step_f32();
 cudaError_t prepare_step_f64();

@@ -19,4 +19,8 @@ cudaError_t launch_fused_f32(const StepLaunch &L, uint32_t nsteps) {
     return L.ctx->inv_tr > 0 ? launch_fused_trunc_f32(L, nsteps) : launch_fused_t<float, false>(L, nsteps);
 }
 cudaError_t launch_push_f32(const StepLaunch &L, double dt) { return launch_push_t<float>(L, dt); }
+cudaError_t launch_wait_check(uint32_t polls, sfq_counters *c, cudaStream_t s) {
+    wait_check_kernel<0><<<1, 32, 0, s>>>(polls, c);
+    return cudaGetLastError();
+}
 }  // namespace sfq

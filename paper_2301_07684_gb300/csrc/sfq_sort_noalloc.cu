@@ -12,6 +12,11 @@
 // needs to start at zero (the sort clears its one accumulator on the stream); the array is
 // shared by every call on a device, so calls that overlap in time on one device race --
 // issue them on one stream or order their streams.
+//
+// The address is kept in the context that looked it up, not in a process-wide table: a
+// context lives no longer than the device context it was created in (its tables are
+// device memory too), so a device reset that reloads the module, and with it the array,
+// cannot leave a stale address behind in a context that is still valid to use.
 #include <mutex>
 
 #include "sfq_internal.h"
@@ -21,9 +26,7 @@ namespace {
 constexpr size_t NOALLOC_BYTES = (size_t)SFQ_SORT_NOALLOC_SCRATCH_BYTES;
 static __device__ __align__(256) unsigned char g_sort_scratch[NOALLOC_BYTES];
 
-constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
-void *g_addr[MAX_DEVICES] = {};
 
 sfq_status fail(sfq_ctx *ctx, sfq_status st, const char *msg) {
     if (ctx) ctx->err = msg;
@@ -43,16 +46,17 @@ struct DeviceGuard {
     }
 };
 
-// Address of the array on the current device (looked up on the first call per device).
-cudaError_t scratch_address(int dev, void **out) {
+// Address of the array on the context's device (current here), looked up on the context's
+// first call and kept in the context.
+cudaError_t scratch_address(sfq_ctx *ctx, void **out) {
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    if (!ctx->noalloc_scratch) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
         if (e != cudaSuccess) return e;
-        g_addr[dev] = p;
+        ctx->noalloc_scratch = p;
     }
-    *out = g_addr[dev];
+    *out = ctx->noalloc_scratch;
     return cudaSuccess;
 }
 
@@ -70,12 +74,11 @@ sfq_status sfq_sort_products_noalloc(sfq_ctx *ctx, const sfq_products *out, int6
     const void *cols[6] = {out->px, out->py, out->pz, out->parent_id, out->step, out->meta};
     for (const void *c : cols)
         if (!c) return fail(ctx, SFQ_ERR_ARG, "null product column");
-    if (ctx->device < 0 || ctx->device >= MAX_DEVICES) return fail(ctx, SFQ_ERR_ARG, "device index out of range");
     if (sfq::sort_scratch_bytes(n, 8) > NOALLOC_BYTES)
         return fail(ctx, SFQ_ERR_ARG, "static sort scratch smaller than the plan for n");
     DeviceGuard g(ctx->device);
     void *scratch = nullptr;
-    cudaError_t e = scratch_address(ctx->device, &scratch);
+    cudaError_t e = scratch_address(ctx, &scratch);
     if (e != cudaSuccess) {
         ctx->err = std::string("sfq_sort_products_noalloc: scratch address: ") + cudaGetErrorString(e);
         return SFQ_ERR_CUDA;

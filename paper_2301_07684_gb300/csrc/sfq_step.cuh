@@ -151,10 +151,13 @@ __device__ __forceinline__ uint64_t od_fill(uint64_t b, uint64_t seed, IdF id_of
     return b;
 }
 // tau_d - R dt in binary64: the binary32 decrement is widened exactly with integer
-// operations and the subtraction is the only binary64 instruction of the update
+// operations and the subtraction is the only binary64 instruction of the update.  A
+// decrement that overflowed binary32 (+inf) is an event, as the binary64 one would be;
+// zero, subnormal and NaN decrements subtract nothing.
 __device__ __forceinline__ bool od_sub(double *tau_ptr, uint64_t b, float d) {
     const uint32_t db = __float_as_uint(d);
-    const uint64_t dd = ((db >> 23) - 1u < 254u) ? f32_to_f64_bits(d) : 0ull;   // normal d > 0, else 0
+    const uint64_t dd = ((db >> 23) - 1u < 254u) ? f32_to_f64_bits(d)                    // normal d > 0
+                                                 : (db == 0x7F800000u ? 0x7FF0000000000000ull : 0ull);
     const double t = __dsub_rn(__longlong_as_double((long long)b), __longlong_as_double((long long)dd));
     // the difference of two non-negative binary64 values is negative exactly when its sign
     // bit is set (it is never -0), so the test runs on the integer pipe

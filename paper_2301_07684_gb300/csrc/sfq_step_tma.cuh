@@ -31,10 +31,10 @@ __device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes) {
                  "r"(bytes)
                  : "memory");
 }
-// Bounded wait for the phase of parity `parity` to complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Bounded wait for the phase of parity `parity` to complete: at most `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit = TMA_WAIT_LIMIT) {
     const uint32_t a = smem_u32(bar);
-    for (uint32_t it = 0; it < TMA_WAIT_LIMIT; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
@@ -93,6 +93,19 @@ constexpr size_t tma_smem_bytes() {
 // A wait that gave up is recorded in the counters.
 __device__ __forceinline__ void raise_timeout(sfq_counters *c) {
     if (c) atomicAdd(&c->timeouts, 1ull);
+}
+
+// Check of the bounded waits: one thread waits, with the kernels' bounded wait, on an
+// mbarrier that nothing completes (one arrival expected, none made), gives up after `polls`
+// polls and records the timeout as the step kernel does.
+template <int = 0>
+__global__ void wait_check_kernel(uint32_t polls, sfq_counters *c) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (!mbar_wait(&bar, 0, polls)) raise_timeout(c);
+    }
 }
 
 template <typename T, int FK, int CW, bool TRUNC = false>
@@ -175,9 +188,17 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
                 }
                 issued_last[s] = t;
             }
-            // before leaving, every copy this warp issued has landed
-            for (int s = 0; s < TMA_NSTAGE; ++s)
-                if (issued_last[s] >= 0) mbar_wait(&full[s], (issued_last[s] / TMA_NSTAGE) & 1);
+            // before leaving, every copy this warp issued has landed; a drain that times out is
+            // counted (the step's results are then invalid) and waited for once more, so that the
+            // block does not exit while its copies may still be writing its shared memory
+            for (int s = 0; s < TMA_NSTAGE; ++s) {
+                if (issued_last[s] < 0) continue;
+                const uint32_t par = (issued_last[s] / TMA_NSTAGE) & 1;
+                if (!mbar_wait(&full[s], par)) {
+                    raise_timeout(a.counters);
+                    mbar_wait(&full[s], par);
+                }
+            }
         }
         return;
     }

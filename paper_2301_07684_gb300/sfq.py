@@ -149,6 +149,10 @@ def lib():
         L.sfq_table_pieces.restype = st
         L.sfq_set_step_shape.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
         L.sfq_set_step_shape.restype = st
+        L.sfq_counters_check.argtypes = [vp]
+        L.sfq_counters_check.restype = st
+        L.sfq_check_bounded_wait.argtypes = [vp, u32, vp, vp]
+        L.sfq_check_bounded_wait.restype = st
         L.sfq_version.restype = C.c_char_p
         _lib = L
     return _lib
@@ -162,7 +166,7 @@ EXPORTED = ["sfq_init", "sfq_finalize", "sfq_last_error", "sfq_constants", "sfq_
             "sfq_mlp_loss_grad", "sfq_mlp_train", "sfq_mlp_predict_lnw", "sfq_mlp_plain_targets", "sfq_mlp_calibrate",
             "sfq_mlp_sample_photon_xi", "sfq_mlp_create_pair", "sfq_mlp_sample_pair_xi",
             "sfq_cascade_run", "sfq_cascade_compact_scratch_bytes", "sfq_cascade_compact", "sfq_set_evaluator",
-            "sfq_table_pieces",
+            "sfq_table_pieces", "sfq_counters_check", "sfq_check_bounded_wait",
             "sfq_version"]
 
 
@@ -186,6 +190,14 @@ def counters_tensor(device="cuda"):
 def counters_dict(t):
     v = t.cpu().tolist()
     return {k: int(v[i]) for i, k in enumerate(COUNTER_NAMES)}
+
+
+def counters_status(t):
+    """sfq_counters_check on a copy of the counters (a device tensor, a host tensor or 16
+    integers): "SFQ_OK", "SFQ_ERR_TIMEOUT", "SFQ_ERR_CAPACITY" or "SFQ_ERR_RANGE"."""
+    import numpy as np
+    h = np.ascontiguousarray(np.asarray(t.cpu() if hasattr(t, "cpu") else t, dtype=np.int64).reshape(16))
+    return STATUS[lib().sfq_counters_check(h.ctypes.data_as(C.c_void_p))]
 
 
 class Context:
@@ -363,6 +375,12 @@ class Context:
         O = products.descriptor()
         self._check(lib().sfq_sort_products_noalloc(self._h, C.byref(O), n, _stream()),
                     "sfq_sort_products_noalloc")
+
+    def check_bounded_wait(self, polls, counters):
+        """sfq_check_bounded_wait: a wait that nothing completes gives up after `polls` polls
+        and adds 1 to counters' timeouts word (counters: a device counters_tensor)."""
+        self._check(lib().sfq_check_bounded_wait(self._h, int(polls), _ptr(counters), _stream()),
+                    "sfq_check_bounded_wait")
 
 
 SORT_NOALLOC_MAX_N = 1 << 20

@@ -81,3 +81,27 @@ def test_binding_argument_counts_match_the_header():
             wrong.append((name, len(at), n))
     assert not wrong, wrong
     assert not unbound, unbound
+
+
+def test_counters_check_maps_the_counters_to_a_status():
+    """sfq_counters_check reads a host copy of the counters only (no device, no context):
+    a timeout outranks dropped records, which outrank inputs outside the fitted range."""
+    from paper_2301_07684_gb300 import sfq
+    names = sfq.COUNTER_NAMES
+
+    def status(**kw):
+        v = [0] * 16
+        for k, x in kw.items():
+            v[names.index(k)] = x
+        return sfq.counters_status(v)
+
+    assert status() == "SFQ_OK"
+    assert status(updates=10, events=3, emitted=3, blcfa_rejected=2, large_rdt=1, gamma_below_one=1) == "SFQ_OK"
+    assert status(dropped=1) == "SFQ_ERR_CAPACITY"
+    assert status(spawn_dropped=4) == "SFQ_ERR_CAPACITY"
+    assert status(out_of_range=2) == "SFQ_ERR_RANGE"
+    assert status(nan_input=1) == "SFQ_ERR_RANGE"
+    assert status(timeouts=1) == "SFQ_ERR_TIMEOUT"
+    assert status(timeouts=1, dropped=5, out_of_range=5) == "SFQ_ERR_TIMEOUT"
+    assert status(dropped=5, out_of_range=5) == "SFQ_ERR_CAPACITY"
+    assert sfq.STATUS[sfq.lib().sfq_counters_check(None)] == "SFQ_ERR_ARG"

@@ -8,7 +8,14 @@ and then the photons (nonlinear Breit-Wheeler by optical depth, Sec. 2 and 4.2);
 pairs are appended both as product records and as stepped children.  Lineages
 (a photon, its pair and the photons the pair emits) are compared with the
 oracle record by record up to their first near-threshold decision (optical depth
-1e-6 tau0, local test 1e-6 r, beyond-LCFA comparisons 1e-4 relative).
+1e-6 tau0, local test 1e-6 r, beyond-LCFA comparisons 1e-4 relative in binary32:
+the threshold of Eq. gammaLCFA comes from the second difference of Eq. condit,
+which in binary32 keeps the force to ~6e-8 but its second difference, about 1/60
+of it at this timestep, only to ~4e-6, and gamma_LCFA ~ delta^(3/2) for large tau/tau_C,
+so gamma_LCFA carries ~6e-6; 1e-4 leaves a margin above that).  The compared
+lineages must include events whose gate held and samples that Eq. rej_cond
+rejected, so that the beyond-LCFA branches are exercised, and the no-emission rule
+of Sec. 5 must never fire (gamma_LCFA <= 0.7 gamma_e).
 """
 import numpy as np
 import pytest
@@ -93,4 +100,46 @@ def test_config3_small(oracle, precision):
     s = compare_lineages(ids, orc, final, prod, TOL[precision], nsteps)
     assert s["records"] > 60, s
     assert s["near"] <= 6, s
+    assert_blcfa_exercised(orc, c)
+    ctx.close()
+
+
+def assert_blcfa_exercised(orc, c):
+    """The compared lineages (no near-threshold decision) went through the gate and the
+    rejection of Eq. rej_cond; the 0.75 gamma_e rule fired nowhere, on either side."""
+    clean = orc["first_near_step"] < 0
+    assert orc["n_gated"][clean].sum() > 0 and orc["n_rejected"][clean].sum() > 0, \
+        (orc["n_gated"][clean].sum(), orc["n_rejected"][clean].sum())
+    assert orc["n_no_emission"].sum() == 0 and c["blcfa_no_emission"] == 0
+    assert c["blcfa_rejected"] > 0
+
+
+@pytest.mark.slow
+def test_config3_full_size(oracle):
+    """Config 3 at its stated size: 2^24 photons, 100 steps, binary32 with a binary64 optical
+    depth; 160 sampled photon lineages (the photon, its pair and the pair's photons)."""
+    import torch
+    from paper_2301_07684_gb300 import build, sfq
+    build.build()
+    ctx = sfq.Context(ref_len_m=W.REF_LEN, dt=W.DT, precision="fp32", seed=77)
+    d = W.config3(n=1 << 24, seed=0)
+    n, nsteps = d["px"].size, d["nsteps"]
+    P, Lp, out, cnt, nlep = run_config3(ctx, d, nsteps, cap_factor=3)   # ~34 records per photon
+    c = sfq.counters_dict(cnt)
+    assert c["dropped"] == 0 and c["spawn_dropped"] == 0 and c["timeouts"] == 0, c
+    assert nlep == 2 * c["pairs"] and out.n() == 2 * c["pairs"] + c["emitted"]
+    ids = W.sample_ids(n, 160, seed=9)
+    orc = oracle_config3(oracle, d, ids, nsteps, ctx.rho, ctx.seed, NEAR["fp32"])
+    sel = torch.as_tensor(ids, device=ctx.device)
+    final = dict(px=P.px[sel].cpu().numpy(), py=P.py[sel].cpu().numpy(), pz=P.pz[sel].cpu().numpy(),
+                 tau=P.tau[sel].cpu().numpy(), flags=P.flags[sel].cpu().numpy())
+    k = out.n()
+    m = torch.isin(out.parent_id[:k], sel)
+    prod = dict(px=out.px[:k][m].cpu().numpy(), py=out.py[:k][m].cpu().numpy(), pz=out.pz[:k][m].cpu().numpy(),
+                parent_id=out.parent_id[:k][m].cpu().numpy().view(np.uint64),
+                step=out.step[:k][m].cpu().numpy().view(np.uint32), meta=out.meta[:k][m].cpu().numpy())
+    s = compare_lineages(ids, orc, final, prod, TOL["fp32"], nsteps)
+    assert s["records"] > 100, s
+    assert s["near"] <= 12, s
+    assert_blcfa_exercised(orc, c)
     ctx.close()

@@ -8,7 +8,12 @@
   photons below chi = 0.01 never convert (the pair rate is zero there, Sec. 4.2); dead
   particles are not updated.
 - Capacity: records beyond the product buffer's capacity are counted as dropped, never
-  written out of bounds, and the count of requested records is exact.
+  written out of bounds, and the count of requested records is exact; sfq_counters_check
+  reports the run as SFQ_ERR_CAPACITY.
+- A decrement R dt that overflows binary32 (+inf) is an event, as its binary64 value is in
+  the oracle.
+- A bounded device wait that gives up is counted, reported as SFQ_ERR_TIMEOUT, and leaves
+  the context usable.
 """
 import numpy as np
 import pytest
@@ -149,4 +154,58 @@ def test_product_capacity_overflow_is_counted():
     assert out.n() == c["emitted"] > cap
     assert c["dropped"] == c["emitted"] - cap
     assert out.px.numel() == guard.numel()
+    assert sfq.counters_status(cnt) == "SFQ_ERR_CAPACITY"
+    ctx.close()
+
+
+def test_overflowing_decrement_is_an_event(oracle):
+    """R dt beyond the binary32 range fires the optical-depth test in binary32 as in the
+    oracle's binary64: every electron emits.  The timestep of 5e35 keeps pref dt finite in
+    binary32 while R dt overflows."""
+    import torch
+    from paper_2301_07684_gb300 import build, sfq
+    build.build()
+    dt = 5e35
+    ctx = sfq.Context(ref_len_m=W.REF_LEN, dt=dt, precision="fp32", seed=3)
+    n = 256
+    g = np.full(n, 3.0)
+    pm = np.sqrt(g * g - 1)
+    chi = np.full(n, 50.0)
+    ey = chi * W.RHO / g                                  # p along x, E along y, B = 0: chi = gamma E / rho
+    T = lambda a, t: torch.as_tensor(np.ascontiguousarray(a)).to(device=ctx.device, dtype=t)
+    P = sfq.ParticleBuffers(T(pm, torch.float32), T(np.zeros(n), torch.float32), T(np.zeros(n), torch.float32),
+                            T(np.ones(n), torch.float64), T(np.full(n, sfq.SFQ_ALIVE, np.uint8), torch.uint8))
+    z = torch.zeros(n, dtype=torch.float32, device=ctx.device)
+    F = sfq.FieldSource.soa(z, T(ey, torch.float32), z, z, z, z)
+    out, cnt = sfq.ProductBuffers(4 * n, torch.float32, ctx.device), sfq.counters_tensor()
+    ctx.mc_step(P, F, 0, out, counters=cnt)
+    torch.cuda.synchronize()
+    c = sfq.counters_dict(cnt)
+    assert c["large_rdt"] == n and c["events"] == n and c["emitted"] == n, c
+    E = np.zeros((n, 1, 6))
+    E[:, 0, 1] = ey.astype(np.float32)                    # the field the device saw
+    orc = oracle.mc_run(np.stack([pm.astype(np.float32), np.zeros(n), np.zeros(n)], 1), np.ones(n),
+                        np.arange(n, dtype=np.uint64), np.full(n, 1, np.uint8), np.zeros(n, np.uint8), E,
+                        rho=ctx.rho, dt=dt, seed=3, nsteps=1)
+    assert np.all(orc["n_events"] == 1)
+    ctx.close()
+
+
+def test_bounded_wait_gives_up_and_is_reported():
+    """A wait on a barrier nothing completes ends after its polls, counts one timeout,
+    sfq_counters_check reports SFQ_ERR_TIMEOUT, and the context keeps working."""
+    import torch
+    from paper_2301_07684_gb300 import sfq
+    ctx = _ctx()
+    cnt = sfq.counters_tensor()
+    ctx.check_bounded_wait(256, cnt)
+    torch.cuda.synchronize()
+    c = sfq.counters_dict(cnt)
+    assert c["timeouts"] == 1 and sfq.counters_status(cnt) == "SFQ_ERR_TIMEOUT"
+    # the context is still usable: a rate call right after
+    g = torch.full((1024,), 1000.0, device=ctx.device)
+    x = torch.full((1024,), 1.0, device=ctx.device)
+    r = ctx.photon_rate(g, x)
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(r).all()) and float(r[0]) > 0
     ctx.close()
