@@ -153,3 +153,41 @@ def test_two_gloo_ranks_equal_the_single_cascade(tmp_path):
     for k in created:
         np.testing.assert_array_equal(got["c_" + k][o1], created[k][o2], err_msg=k)
 
+
+
+def _synthetic_records(rank, k):
+    """k random records of rank (parent ids over the whole unsigned range, so that ids with
+    bit 63 set -- a cascade's created particles -- are ordered as unsigned)."""
+    g = np.random.default_rng(100 + rank)
+    return dict(px=g.standard_normal(k).astype(np.float32), py=g.standard_normal(k).astype(np.float32),
+                pz=g.standard_normal(k).astype(np.float32),
+                parent_id=g.integers(0, 2 ** 63, k, dtype=np.uint64) * np.uint64(2) + np.uint64(rank),
+                step=g.integers(0, 1 << 31, k, dtype=np.uint32) * np.uint32(2),
+                meta=g.integers(0, 256, k, dtype=np.uint8))
+
+
+def _big_worker(rank, world, port, out_dir):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    k = (1 << 20) - 12345 * rank
+    merged, total = shard.gather(_synthetic_records(rank, k), {"records": k, "events": 3 * k})
+    if rank == 0:
+        np.savez(os.path.join(out_dir, "big.npz"), **merged, records=total["records"], events=total["events"])
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_gather_of_a_million_records_per_rank(tmp_path):
+    """The tensor gather (counts, then padded columns) at 2^20 records per rank with unequal
+    counts: the union in (parent id, step, member, tag) order, counters summed."""
+    import torch.multiprocessing as mp
+    port = _free_port()
+    mp.start_processes(_big_worker, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    got = np.load(tmp_path / "big.npz")
+    ks = [(1 << 20) - 12345 * r for r in range(2)]
+    ref = shard.merge_records([_synthetic_records(r, ks[r]) for r in range(2)])
+    assert int(got["records"]) == sum(ks) and int(got["events"]) == 3 * sum(ks)
+    for k in shard.RECORD_COLUMNS:
+        np.testing.assert_array_equal(got[k], ref[k], err_msg=k)
