@@ -132,12 +132,15 @@ def time_mc(sfq, torch, ctx, P, fields_for_step, steps, warmup, out, counters, n
     """W warm-up steps (0..W-1), then timed regions of exactly `steps` steps (W..W+K-1), each
     bracketed by a barrier and a device synchronisation; CUDA events around each launch and
     around each region on the launching stream.  With `reset` every region starts from the
-    same state (reset() restores it, outside the timed region), so all regions do the same
-    work; at least `min_repeats` regions, more until `min_total_ms` of timed work.
+    state after the warm-up steps (reset(capture=True) keeps it, reset() restores it, outside
+    the timed region), so all regions do the same work; at least `min_repeats` regions, more
+    until `min_total_ms` of timed work.
     Returns (region_ms list, launch_ms list of every launch of every region)."""
     stream = torch.cuda.current_stream()
     for s in range(warmup):
         ctx.mc_step(P, fields_for_step(s), s, out, counters=counters)
+    if reset is not None:
+        reset(capture=True)                         # the state after the warm-up steps
     regions, launch_ms = [], []
     n_regions = None
     while True:
@@ -234,9 +237,12 @@ def run_ours(args):
             tuned = (v, sh, None)
         else:
             tuned = ctx.autotune_step(P, fs(0), 0)
-        init = [t.clone() for t in (P.px, P.py, P.pz, P.tau, P.flags)]
+        init = []
 
-        def reset():
+        def reset(capture=False):
+            if capture:
+                init[:] = [t.clone() for t in (P.px, P.py, P.pz, P.tau, P.flags)]
+                return
             for dst, src in zip((P.px, P.py, P.pz, P.tau, P.flags), init):
                 dst.copy_(src)
 
@@ -956,7 +962,8 @@ def oracle_config3_sample(n_photons, nsteps):
 
 def oracle_replay(rep):
     """The oracle replays sampled lineages of the timed run: the same particles from the same
-    initial state over the same steps (W .. W+K-1), fields and Philox key.  Returns
+    initial state over the warm-up and timed steps (0 .. W+K-1), fields and Philox key, and
+    compares the timed steps W .. W+K-1.  Returns
     (updates, seconds, threads, parity), parity comparing the oracle's decisions (the steps
     at which each lineage emitted) with the records the GPU wrote in its last timed region:
     lineages whose decisions match, lineages cut at a near-threshold decision (|tau_d| <=
@@ -967,14 +974,14 @@ def oracle_replay(rep):
     O.build()
     d, fin, K, s0 = rep["d"], rep["final"], rep["steps"], rep["warmup"]
     ids = np.asarray(fin["ids"], np.int64)
-    E = np.zeros((ids.size, K, 6))
-    for j in range(K):
-        (_, ey, _), (_, _, bz) = W.plane_wave_fields(d["k0"][ids], d["amp0"], d["table"], s0 + j)
+    E = np.zeros((ids.size, s0 + K, 6))
+    for j in range(s0 + K):
+        (_, ey, _), (_, _, bz) = W.plane_wave_fields(d["k0"][ids], d["amp0"], d["table"], j)
         E[:, j, 1], E[:, j, 5] = ey, bz
     p = np.stack([d["px"][ids], d["py"][ids], d["pz"][ids]], 1).astype(np.float64)
     t = time.perf_counter()
     orc = O.mc_run(p, d["tau"][ids], ids.astype(np.uint64), d["flags"][ids], np.zeros(ids.size, np.uint8), E,
-                   rho=W.RHO, dt=W.DT, seed=rep["seed"], step0=s0, nsteps=K, near_od=1e-6)
+                   rho=W.RHO, dt=W.DT, seed=rep["seed"], step0=0, nsteps=s0 + K, near_od=1e-6)
     sec = time.perf_counter() - t
     op, gr = orc["products"], fin["records"]
     near = mism = 0
@@ -982,7 +989,8 @@ def oracle_replay(rep):
     for j, pid in enumerate(ids.tolist()):
         cut = orc["first_near_step"][j] if orc["first_near_step"][j] >= 0 else s0 + K
         near += orc["first_near_step"][j] >= 0
-        mo = np.nonzero((op["parent_id"] == pid) & (op["step"] < cut))[0]
+        # the timed region's records are those of steps W ... W+K-1
+        mo = np.nonzero((op["parent_id"] == pid) & (op["step"] >= s0) & (op["step"] < cut))[0]
         mg = np.nonzero((gr["parent_id"] == pid) & (gr["step"] < cut))[0]
         so, sg = np.sort(op["step"][mo]), np.sort(gr["step"][mg])
         if not np.array_equal(so, sg):
@@ -997,14 +1005,15 @@ def oracle_replay(rep):
               "near_threshold_lineages": int(near), "decision_mismatches": int(mism),
               "max_record_rel_diff": worst,
               "protocol": "decisions compared up to the first near-threshold one (|tau_d| <= 1e-6 tau0)"}
-    return ids.size * K, sec, O.num_threads(), parity
+    return ids.size * (s0 + K), sec, O.num_threads(), parity
 
 
 def cpu_baseline(args, replay=None):
     if replay is not None:
         upd, sec, thr, parity = oracle_replay(replay)
-        sample = (f"{len(replay['final']['ids'])} sampled particles x {replay['steps']} steps of the timed run, "
-                  f"replayed from its initial state ({upd} updates in {sec:.1f} s)")
+        sample = (f"{len(replay['final']['ids'])} sampled particles of the timed run over its "
+                  f"{replay['warmup']} + {replay['steps']} steps, replayed from the initial state "
+                  f"({upd} updates in {sec:.1f} s)")
     else:
         upd, sec, thr = oracle_sample_run(args.oracle_particles, args.oracle_steps)
         parity = None

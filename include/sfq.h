@@ -470,6 +470,35 @@ sfq_status sfq_mlp_create_pair(sfq_ctx *ctx, uint64_t seed, sfq_mlp **out);
 sfq_status sfq_mlp_sample_pair_xi(sfq_mlp *m, int64_t n, const void *chi, const void *r, void *xi_e, void *xi_p,
                                   int32_t use_flags, struct sfq_counters *counters, void *stream);
 
+/* The Monte Carlo step with the photon surrogate on its event path (the survey's
+ * use_surrogate; the paper has no surrogate).  Caller-owned queue of photon-emission
+ * events (device pointers, `capacity` entries each, 16-byte aligned): */
+typedef struct {
+    int64_t capacity;
+    int64_t *index;            /* int64: the emitter's index in the stepped population */
+    float *chi, *r;            /* binary32: chi at the event and the energy draw r_1 (word 1) */
+    float *gamma;              /* binary32: the emitter's energy before the event */
+    float *px, *py, *pz;       /* binary32: its momentum before the event */
+    float *xi;                 /* binary32: the fraction the surrogate pass sampled (output) */
+    unsigned long long *count; /* device counter of requested entries; each step zeroes it */
+} sfq_event_queue;
+/* Attach a trained photon surrogate (binary32 context, the object's own context) and a
+ * queue, or detach with net == NULL.  While attached, every sfq_mc_step (and sfq_mc_run)
+ * of the context runs photon emission by the optical-depth method (Sec. 2, 4.1) in three
+ * launches on the step's stream: the step kernel decides the events as without the
+ * surrogate (the decision does not depend on the sampler) and appends each emission to
+ * the queue instead of sampling it; the tensor-core surrogate samples xi = s/(1 + s) for
+ * the queued events (Eq. again through the network; with use_flags, flagged cells and chi
+ * outside [1e-3, 100] take the plain sampler, counted in surrogate_fallbacks); a finishing
+ * pass applies the recoil and appends the photon records (Sec. 3, collinear).  Events past
+ * the queue's capacity are sampled by the plain sampler in the step kernel (also counted
+ * in surrogate_fallbacks).  Pair creation, beyond-LCFA leptons, sfq_mc_run_fused and
+ * sfq_cascade_run keep the plain samplers.  After a step the queue holds that step's
+ * emissions (index, chi, r, gamma, momentum and the sampled xi), in no particular order.
+ * use_flags requires sfq_mlp_calibrate first.  SFQ_ERR_ARG for a binary64 context, a pair
+ * surrogate, a net of another context, or NULL/misaligned queue buffers. */
+sfq_status sfq_set_surrogate(sfq_ctx *ctx, sfq_mlp *net, const sfq_event_queue *queue, int32_t use_flags);
+
 /* Launch shape of sfq_mc_step for this context, the knob the autotuner turns.
  *   variant: 0 = automatic; 1 = warp-streaming kernel (each warp loads its particles
  *            directly); 2 = TMA-staged kernel (bulk copies of each tile into shared

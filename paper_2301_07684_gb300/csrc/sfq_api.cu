@@ -114,6 +114,13 @@ cudaError_t launch_step(const sfq_ctx *ctx, const sfq_particles *p, const sfq_fi
     if (p->n == 0) return cudaSuccess;
     const int ppt = ctx->step_ppt ? ctx->step_ppt : (ctx->cfg.precision == SFQ_FP64 ? 1 : 2);
     StepLaunch L{ctx, p, f, step, out, spawn, counters, stream, ctx->step_grid, ppt, ctx->step_variant, cascade};
+    if (ctx->surr && !cascade && ctx->cfg.precision == SFQ_FP32 && p->lepton_model == SFQ_LEPTON_LCFA_OD) {
+        // photon emissions through the surrogate: queue them, then sample and finish them
+        cudaError_t e = cudaMemsetAsync(ctx->surr_q.count, 0, sizeof(unsigned long long), stream);
+        if (e == cudaSuccess) e = launch_step_surr_f32(L);
+        if (e == cudaSuccess) e = launch_surrogate_apply(ctx, p, step, out, counters, stream);
+        return e;
+    }
     return ctx->cfg.precision == SFQ_FP64 ? launch_step_f64(L) : launch_step_f32(L);
 }
 
@@ -462,6 +469,7 @@ sfq_status sfq_set_sampler_coefficients(sfq_ctx *ctx, int32_t k) {
     if (!ctx) return SFQ_ERR_ARG;
     const int n = sfq::inv_coefficients(ctx->cfg.precision);
     if (k < n - 2 || k > n) return fail(ctx, SFQ_ERR_ARG, "coefficients per variable must be n, n - 1 or n - 2");
+    if (k < n && ctx->surr) return fail(ctx, SFQ_ERR_ARG, "truncated samplers with a surrogate attached");
     if (k < n && ctx->eval == SFQ_EVAL_CLENSHAW)
         return fail(ctx, SFQ_ERR_ARG, "truncated samplers need the Horner evaluator");
     const int tr = n - k;

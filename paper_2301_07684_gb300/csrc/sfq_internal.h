@@ -27,6 +27,11 @@ struct sfq_ctx {
     void *d_nlc_rate_ch = nullptr, *d_nbw_rate_ch = nullptr;   // Chebyshev pieces (Clenshaw evaluator)
     void *d_nlc_inv_ch = nullptr, *d_nbw_inv_ch = nullptr;
     void *noalloc_scratch = nullptr;   // address of the no-allocation sort's array on this context's device
+    // the photon surrogate on the step's event path (sfq_set_surrogate)
+    sfq_mlp *surr = nullptr;
+    sfq_event_queue surr_q{};
+    int surr_flags = 0;
+    int surr_per_sm = 1;
     std::string err;
 };
 
@@ -84,6 +89,12 @@ cudaError_t launch_push_f32(const StepLaunch &, double dt);
 cudaError_t launch_push_f64(const StepLaunch &, double dt);
 // the same with the truncated samplers compiled in (sfq_launch_tr_f32.cu / _f64.cu)
 cudaError_t launch_step_trunc_f32(const StepLaunch &);
+// The step kernels whose photon emissions go to the surrogate's queue (sfq_launch_surr_f32.cu),
+// and the surrogate pass that samples and finishes them (sfq_mlp.cu).
+cudaError_t launch_step_surr_f32(const StepLaunch &);
+cudaError_t prepare_step_surr_f32();
+cudaError_t launch_surrogate_apply(const sfq_ctx *ctx, const sfq_particles *p, uint32_t step, const sfq_products *out,
+                                   sfq_counters *counters, cudaStream_t stream);
 cudaError_t launch_step_trunc_f64(const StepLaunch &);
 cudaError_t launch_fused_trunc_f32(const StepLaunch &, uint32_t nsteps);
 cudaError_t launch_fused_trunc_f64(const StepLaunch &, uint32_t nsteps);

@@ -289,29 +289,31 @@ __device__ __forceinline__ void boris(T u[3], const T E[3], const T B[3], T q, T
 // ---------------------------------------------------------------------------
 // Counters: per-thread registers, reduced per block, one atomic per counter.
 struct Cnt {
-    uint32_t v[12];     // per-thread counts of one launch (fit in 32 bits); widened when flushed
+    uint32_t v[13];     // per-thread counts of one launch (fit in 32 bits); widened when flushed
     __device__ void zero() {
 #pragma unroll
-        for (int k = 0; k < 12; ++k) v[k] = 0;
+        for (int k = 0; k < 13; ++k) v[k] = 0;
     }
 };
-enum { C_UPD, C_EV, C_EMIT, C_PAIR, C_DROP, C_SDROP, C_OOR, C_NAN, C_G1, C_RDT, C_NOEM, C_REJ };
+// v[k] goes to word k of sfq_counters for k < 12; C_SURR (surrogate fallbacks) to word 13
+enum { C_UPD, C_EV, C_EMIT, C_PAIR, C_DROP, C_SDROP, C_OOR, C_NAN, C_G1, C_RDT, C_NOEM, C_REJ, C_SURR };
 
 __device__ __forceinline__ void flush_counters(Cnt &c, sfq_counters *out) {
     if (!out) return;
-    __shared__ unsigned long long red[12];
-    if (threadIdx.x < 12) red[threadIdx.x] = 0;
+    __shared__ unsigned long long red[13];
+    if (threadIdx.x < 13) red[threadIdx.x] = 0;
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
+    for (int k = 0; k < 13; ++k) {
         unsigned long long s = (unsigned long long)c.v[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
         if ((threadIdx.x & 31) == 0 && s) atomicAdd(&red[k], s);
     }
     __syncthreads();
-    if (threadIdx.x < 12 && red[threadIdx.x])
-        atomicAdd(reinterpret_cast<unsigned long long *>(out) + threadIdx.x, red[threadIdx.x]);
+    if (threadIdx.x < 13 && red[threadIdx.x])
+        atomicAdd(reinterpret_cast<unsigned long long *>(out) + (threadIdx.x < 12 ? threadIdx.x : 13),
+                  red[threadIdx.x]);
 }
 
 // ---------------------------------------------------------------------------

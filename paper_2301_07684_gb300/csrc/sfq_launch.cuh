@@ -162,6 +162,14 @@ static StepArgs<T> make_step_args(const StepLaunch &L) {
     a.pair_chi_min = (T)ctx->pair_chi_min;
     a.tab = tables_of<T>(ctx);
     a.counters = L.counters;
+    if (ctx->surr) {
+        const sfq_event_queue &q = ctx->surr_q;
+        a.qcap = q.capacity;
+        a.qidx = q.index;
+        a.qchi = q.chi; a.qr = q.r; a.qg = q.gamma;
+        a.qpx = q.px; a.qpy = q.py; a.qpz = q.pz;
+        a.qcount = q.count;
+    }
     return a;
 }
 

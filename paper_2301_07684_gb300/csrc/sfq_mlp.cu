@@ -51,6 +51,16 @@ constexpr int NCX = 64, NCU = 64, NCELL = NCX * NCU;   // calibration cells in (
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ float qz(float x, bool q) { return q ? bf16r(x) : x; }
 __device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
+// SiLU of the inference paths (tensor-core kernel, SIMT reference and calibration) with one
+// special-function instruction: z sigma(z) = h (1 + tanh h), h = z / 2, from
+// sigma(z) = (1 + tanh(z/2)) / 2.  tanh.approx.f32 has a relative error below 2^-10.987
+// (PTX ISA), which is below the bfloat16 rounding the activations then get (2^-9).
+// `h` is passed in: the callers form it as 0.5 z + 0.5 b in one fma from halved biases.
+__device__ __forceinline__ float silu_h(float h) {
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(h));
+    return fmaf(h, t, h);
+}
 __device__ __forceinline__ float dsilu(float z) {
     const float s = __fdividef(1.0f, 1.0f + __expf(-z));
     return s * (1.0f + z * (1.0f - s));
@@ -363,20 +373,23 @@ __device__ __forceinline__ float forward_simt(const SimtW &W, const Kind &K, flo
     features(K, chi, u, x1, x2);
     float a[H], b[H];
 #pragma unroll
-    for (int j = 0; j < H; ++j) a[j] = bf16r(silu(fmaf(W.w1[2 * j], x1, fmaf(W.w1[2 * j + 1], x2, W.b1[j]))));
+    for (int j = 0; j < H; ++j)
+        a[j] = bf16r(silu_h(0.5f * fmaf(W.w1[2 * j], x1, fmaf(W.w1[2 * j + 1], x2, W.b1[j]))));
+    // layers 2 and 3: the products summed in binary32 (the tensor cores' order differs), then
+    // h = (sum + b) / 2 as the tensor-core epilogue forms it
 #pragma unroll
     for (int j = 0; j < H; ++j) {
-        float acc = W.b2[j];
+        float acc = 0.0f;
 #pragma unroll
         for (int k = 0; k < H; ++k) acc = fmaf(a[k], W.w2[j * H + k], acc);
-        b[j] = bf16r(silu(acc));
+        b[j] = bf16r(silu_h(fmaf(0.5f, acc, 0.5f * W.b2[j])));
     }
 #pragma unroll
     for (int j = 0; j < H; ++j) {
-        float acc = W.b3[j];
+        float acc = 0.0f;
 #pragma unroll
         for (int k = 0; k < H; ++k) acc = fmaf(b[k], W.w3[j * H + k], acc);
-        a[j] = bf16r(silu(acc));
+        a[j] = bf16r(silu_h(fmaf(0.5f, acc, 0.5f * W.b3[j])));
     }
     float y = W.b4;
 #pragma unroll
@@ -521,21 +534,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
 }
 // Row m of a 128 x 64 (or 64 x 64) K-major operand: 8 chunks of 8 bf16 (16 bytes).
 __device__ __forceinline__ uint32_t row_chunk_offset(int m, int j) { return (uint32_t)((((m >> 3) * 8) + j) * 128 + (m & 7) * 16); }
-__device__ __forceinline__ void store_row_bf16(unsigned char *base, int m, const float *a) {
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        uint4 v;
-        __nv_bfloat162 p0 = __floats2bfloat162_rn(a[8 * j + 0], a[8 * j + 1]);
-        __nv_bfloat162 p1 = __floats2bfloat162_rn(a[8 * j + 2], a[8 * j + 3]);
-        __nv_bfloat162 p2 = __floats2bfloat162_rn(a[8 * j + 4], a[8 * j + 5]);
-        __nv_bfloat162 p3 = __floats2bfloat162_rn(a[8 * j + 6], a[8 * j + 7]);
-        v.x = *reinterpret_cast<uint32_t *>(&p0);
-        v.y = *reinterpret_cast<uint32_t *>(&p1);
-        v.z = *reinterpret_cast<uint32_t *>(&p2);
-        v.w = *reinterpret_cast<uint32_t *>(&p3);
-        *reinterpret_cast<uint4 *>(base + row_chunk_offset(m, j)) = v;
-    }
-}
+// The finishing of queued photon emissions (APPLY): the emitter's state before the event,
+// its population, and the product records (sfq_set_surrogate).
+struct ApplyOut {
+    const int64_t *idx;
+    const float *g, *px, *py, *pz;
+    float *ppx, *ppy, *ppz;
+    uint8_t *flags;
+    const uint64_t *id;
+    uint64_t id_base;
+    int64_t cap;
+    float *opx, *opy, *opz;
+    uint64_t *opid;
+    uint32_t *ostep;
+    uint8_t *ometa;
+    unsigned long long *ocount;
+    uint32_t step;
+};
 
 struct InferArgs {
     const float *params;
@@ -547,30 +562,89 @@ struct InferArgs {
     sfq_counters *counters;
     int *status;              // set to 1 when a bounded wait gave up
     Kind K;                   // photon: xi, xi_c = 1 - xi; pair: xi = electron share, xi_c = positron share
+    const unsigned long long *n_dev;   // APPLY: device count of queued samples (min with n)
+    ApplyOut ap;
 };
+
+// Warp-wide reservation of one slot per lane that wants one: one atomic per warp.
+__device__ __forceinline__ unsigned long long warp_reserve(unsigned long long *ctr, bool want) {
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, want);
+    const int lane = threadIdx.x & 31;
+    const int leader = m ? __ffs(m) - 1 : 0;
+    unsigned long long base = 0;
+    if (m && lane == leader) base = atomicAdd(ctr, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    return base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
+}
 
 constexpr uint32_t SM_A = 0, SM_B2 = 16384, SM_B3 = 24576, SM_SMALL = 32768;
 constexpr uint32_t SM_FLAGS = SM_SMALL + (H * 2 + 4 * H + 4) * 4;
 constexpr uint32_t SM_BYTES = SM_FLAGS + NCELL;
 constexpr uint32_t INFER_SMEM = SM_BYTES + 1024;     // + alignment slack
+constexpr int INFER_MINB = 4;                         // resident blocks per SM the registers allow
 
-__global__ void __launch_bounds__(IT) infer_tc_kernel(const InferArgs a) {
+// Eight bfloat16 (one 16-byte K chunk of an operand row) from eight binary32 values.
+__device__ __forceinline__ uint4 pack8_bf16(const float *a) {
+    uint4 v;
+    __nv_bfloat162 p0 = __floats2bfloat162_rn(a[0], a[1]);
+    __nv_bfloat162 p1 = __floats2bfloat162_rn(a[2], a[3]);
+    __nv_bfloat162 p2 = __floats2bfloat162_rn(a[4], a[5]);
+    __nv_bfloat162 p3 = __floats2bfloat162_rn(a[6], a[7]);
+    v.x = *reinterpret_cast<uint32_t *>(&p0);
+    v.y = *reinterpret_cast<uint32_t *>(&p1);
+    v.z = *reinterpret_cast<uint32_t *>(&p2);
+    v.w = *reinterpret_cast<uint32_t *>(&p3);
+    return v;
+}
+
+// The epilogue of a tensor-core layer for this thread's row, 32 accumulator columns at a
+// time (so that no more than 32 accumulators are live): h = (d + b) / 2 from the halved
+// biases hb, SiLU, and either the bfloat16 row of the next layer's operand A (to_a) or the
+// output layer's dot product with w4 (acc).
+__device__ __forceinline__ void epilogue(uint32_t t_row, const float *hb, unsigned char *a_base, int row, bool to_a,
+                                         const float *w4, float &acc) {
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        float d[32];
+        tmem_ld32(t_row + 32 * half, d);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) d[j] = silu_h(fmaf(0.5f, d[j], hb[32 * half + j]));
+        if (to_a) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                *reinterpret_cast<uint4 *>(a_base + row_chunk_offset(row, 4 * half + c)) = pack8_bf16(d + 8 * c);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc = fmaf(bf16r(d[j]), w4[32 * half + j], acc);
+        }
+    }
+}
+
+// One block of 128 threads walks over tiles of 128 samples (one sample per thread, one
+// row of the 128 x 64 activation tile); INFER_MINB blocks share an SM, so that the tensor
+// cores of one block's layer run while the others compute their SiLU epilogues.
+// APPLY (photon kind): the samples are the queued emissions of a Monte Carlo step; each
+// sampled xi also recoils its emitter (Sec. 3: the lepton keeps (1 - xi) gamma along its
+// direction) and appends the collinear photon's record.
+template <bool APPLY>
+__global__ void __launch_bounds__(IT, INFER_MINB) infer_tc_kernel(const InferArgs a) {
     extern __shared__ unsigned char sraw[];
     __shared__ uint64_t mbar;
     __shared__ uint32_t tmem_base;
     __shared__ int s_err;
-    __shared__ unsigned long long s_cnt[3];
+    __shared__ unsigned long long s_cnt[6];
     // 1024-byte aligned operand area
     const uint32_t raw = s_u32(sraw);
     unsigned char *sm = sraw + ((1024u - (raw & 1023u)) & 1023u);
     const uint32_t sbase = s_u32(sm);
     float *w1 = reinterpret_cast<float *>(sm + SM_SMALL);
-    float *b1 = w1 + 2 * H, *b2 = b1 + H, *b3 = b2 + H, *w4 = b3 + H, *b4 = w4 + H;
+    float *b1 = w1 + 2 * H, *hb2 = b1 + H, *hb3 = hb2 + H, *w4 = hb3 + H, *b4 = w4 + H;
     uint8_t *fl = sm + SM_FLAGS;
     const int tid = threadIdx.x, warp = tid >> 5;
     const float *P = a.params;
 
-    // weights: W2, W3 as bf16 in the K-major core-matrix layout; the rest binary32
+    // weights: W2, W3 as bf16 in the K-major core-matrix layout; layer 1 and 4 binary32
+    // (bf16-rounded weights); the biases of layers 2 and 3 halved for the SiLU form
     for (int e = tid; e < H * H; e += IT) {
         const int n_ = e >> 6, k = e & 63;
         const uint32_t off = row_chunk_offset(n_, k >> 3) + (k & 7) * 2;
@@ -581,13 +655,13 @@ __global__ void __launch_bounds__(IT) infer_tc_kernel(const InferArgs a) {
         w1[2 * e] = bf16r(P[O_W1 + 2 * e]);
         w1[2 * e + 1] = bf16r(P[O_W1 + 2 * e + 1]);
         b1[e] = P[O_B1 + e];
-        b2[e] = P[O_B2 + e];
-        b3[e] = P[O_B3 + e];
+        hb2[e] = 0.5f * P[O_B2 + e];
+        hb3[e] = 0.5f * P[O_B3 + e];
         w4[e] = bf16r(P[O_W4 + e]);
     }
     if (tid == 0) *b4 = P[O_B4];
     for (int e = tid; e < NCELL; e += IT) fl[e] = a.flags ? a.flags[e] : 0;
-    if (tid < 3) s_cnt[tid] = 0;
+    if (tid < 6) s_cnt[tid] = 0;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_u32(&tmem_base)),
                      "r"(TMEM_COLS)
@@ -605,13 +679,18 @@ __global__ void __launch_bounds__(IT) infer_tc_kernel(const InferArgs a) {
     const uint32_t taddr = tmem_base;
     const uint32_t t_row = taddr + ((uint32_t)(warp * 32) << 16);
     uint32_t phase = 0;
-    uint32_t n_nan = 0, n_oor = 0, n_fb = 0;
-    const int64_t ntiles = (a.n + IT - 1) / IT;
+    uint32_t n_nan = 0, n_oor = 0, n_fb = 0, n_emit = 0, n_drop = 0, n_g1 = 0;
+    int64_t n_all = a.n;
+    if (APPLY) {
+        const int64_t q = (int64_t)*a.n_dev;
+        n_all = q < n_all ? q : n_all;
+    }
+    const int64_t ntiles = (n_all + IT - 1) / IT;
     int pending = 0;                              // an MMA group issued and not yet waited for
 
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t i = tile * IT + tid;
-        const bool valid = i < a.n;
+        const bool valid = i < n_all;
         const float chi = valid ? a.chi[i] : 1.0f;
         const float r = valid ? a.r[i] : 0.5f;
         const bool bad = !(chi >= 0.0f) || !(r > 0.0f) || !(r < 1.0f);
@@ -619,14 +698,20 @@ __global__ void __launch_bounds__(IT) infer_tc_kernel(const InferArgs a) {
         const float u = a.K.pair ? fabsf(rp) : r;
         const bool in_range = chi >= a.K.chi_lo && chi <= a.K.chi_hi;
         const bool fallback = !bad && (!in_range || fl[cell_of(a.K, chi, u)]);
-        // layer 1 on the CUDA cores (binary32 features, bf16-rounded weights)
+        // layer 1 on the CUDA cores (binary32 features, bf16-rounded weights), 8 columns at a time
         float x1, x2;
         features(a.K, in_range ? chi : 1.0f, bad ? 0.5f : u, x1, x2);
-        float v[H];
 #pragma unroll
-        for (int j = 0; j < H; ++j) v[j] = silu(fmaf(w1[2 * j], x1, fmaf(w1[2 * j + 1], x2, b1[j])));
-        store_row_bf16(sm + SM_A, tid, v);
-        float y = 0.0f;
+        for (int c = 0; c < 8; ++c) {
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int j = 8 * c + q;
+                v[q] = silu_h(0.5f * fmaf(w1[2 * j], x1, fmaf(w1[2 * j + 1], x2, b1[j])));
+            }
+            *reinterpret_cast<uint4 *>(sm + SM_A + row_chunk_offset(tid, c)) = pack8_bf16(v);
+        }
+        float y = *b4;
 #pragma unroll 1
         for (int layer = 0; layer < 2; ++layer) {
             fence_async_smem();
@@ -647,23 +732,13 @@ __global__ void __launch_bounds__(IT) infer_tc_kernel(const InferArgs a) {
             pending = 0;
             phase ^= 1;
             tc_fence_after();
-            float d[H];
-            tmem_ld32(t_row, d);
-            tmem_ld32(t_row + 32, d + 32);
-            const float *bb = layer == 0 ? b2 : b3;
-            if (layer == 0) {
-#pragma unroll
-                for (int j = 0; j < H; ++j) v[j] = silu(d[j] + bb[j]);
-                store_row_bf16(sm + SM_A, tid, v);     // the MMA that read A has completed
-            } else {
-                float acc = *b4;
-#pragma unroll
-                for (int j = 0; j < H; ++j) acc = fmaf(bf16r(silu(d[j] + bb[j])), w4[j], acc);
-                y = acc;
-            }
+            // layer 2: the SiLU row goes to A (the MMA that read A has completed); layer 3:
+            // the output layer's dot product
+            epilogue(t_row, layer == 0 ? hb2 : hb3, sm + SM_A, tid, layer == 0, w4, y);
             tc_fence_before();
         }
         if (s_err) break;
+        float xi_v = 0.0f, xc_v = 0.0f;
         if (valid) {
             float xi, xc;
             if (bad) {
@@ -697,6 +772,41 @@ __global__ void __launch_bounds__(IT) infer_tc_kernel(const InferArgs a) {
             }
             a.xi[i] = xi;
             if (a.xi_c) a.xi_c[i] = xc;
+            xi_v = xi;
+            xc_v = xc;
+        }
+        if (APPLY) {
+            // recoil of the emitter and the photon's record (every lane takes part in the
+            // warp-wide reservation)
+            const ApplyOut &o = a.ap;
+            const bool emit = valid && !bad;
+            const unsigned long long slot = warp_reserve(o.ocount, emit);
+            if (emit) {
+                // xi and 1 - xi = 1/(1 + s), the latter with relative precision (hard photons)
+                const float xi = xi_v, xc = xc_v;
+                const int64_t e = o.idx[i];
+                const float g = o.g[i], px = o.px[i], py = o.py[i], pz = o.pz[i];
+                const float pm = sqrtf(fmaf(px, px, fmaf(py, py, pz * pz)));
+                const float inv_pm = pm > 0.0f ? 1.0f / pm : 0.0f;
+                const float nx = px * inv_pm, ny = py * inv_pm, nz = pz * inv_pm;
+                const float gph = g * xi, gnew = g * xc;
+                const float q2 = fmaf(gnew, gnew, -1.0f);
+                const float pnew = q2 > 0.0f ? sqrtf(q2) : 0.0f;
+                n_g1 += !(q2 > 0.0f);
+                const uint8_t fl = o.flags[e];
+                if (slot < (unsigned long long)o.cap) {
+                    o.opx[slot] = nx * gph; o.opy[slot] = ny * gph; o.opz[slot] = nz * gph;
+                    o.opid[slot] = o.id ? o.id[e] : o.id_base + (uint64_t)e;
+                    o.ostep[slot] = o.step;
+                    o.ometa[slot] = (uint8_t)(SFQ_PHOTON | (((fl >> SFQ_TAG_SHIFT) & 3u) << 4));
+                } else {
+                    ++n_drop;
+                }
+                o.ppx[e] = nx * pnew; o.ppy[e] = ny * pnew; o.ppz[e] = nz * pnew;
+                // a lepton left without momentum leaves the step (as in the step kernels)
+                if (!(pnew > 0.0f)) o.flags[e] = (uint8_t)(fl & ~SFQ_ALIVE);
+                ++n_emit;
+            }
         }
     }
     // a group whose wait gave up: wait once more (bounded) before the tensor memory is freed
@@ -707,6 +817,11 @@ __global__ void __launch_bounds__(IT) infer_tc_kernel(const InferArgs a) {
     atomicAdd(&s_cnt[0], (unsigned long long)n_nan);
     atomicAdd(&s_cnt[1], (unsigned long long)n_oor);
     atomicAdd(&s_cnt[2], (unsigned long long)n_fb);
+    if (APPLY) {
+        atomicAdd(&s_cnt[3], (unsigned long long)n_emit);
+        atomicAdd(&s_cnt[4], (unsigned long long)n_drop);
+        atomicAdd(&s_cnt[5], (unsigned long long)n_g1);
+    }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -717,11 +832,59 @@ __global__ void __launch_bounds__(IT) infer_tc_kernel(const InferArgs a) {
         if (s_cnt[0]) atomicAdd(&a.counters->nan_input, s_cnt[0]);
         if (s_cnt[1]) atomicAdd(&a.counters->out_of_range, s_cnt[1]);
         if (s_cnt[2]) atomicAdd(&a.counters->surrogate_fallbacks, s_cnt[2]);
+        if (APPLY) {
+            if (s_cnt[3]) atomicAdd(&a.counters->emitted, s_cnt[3]);
+            if (s_cnt[4]) atomicAdd(&a.counters->dropped, s_cnt[4]);
+            if (s_cnt[5]) atomicAdd(&a.counters->gamma_below_one, s_cnt[5]);
+        }
     }
     if (s_err && tid == 0 && a.status) atomicExch(a.status, 1);
 }
 
 }  // namespace mlp
+
+// The surrogate pass of a step: sample the queued emissions and finish them (recoil and
+// records), one persistent grid over the queue's capacity (the count is read on the device).
+cudaError_t launch_surrogate_apply(const sfq_ctx *ctx, const sfq_particles *p, uint32_t step, const sfq_products *out,
+                                   sfq_counters *counters, cudaStream_t stream) {
+    using namespace mlp;
+    const sfq_mlp *m = ctx->surr;
+    const sfq_event_queue &q = ctx->surr_q;
+    if (q.capacity <= 0) return cudaSuccess;
+    const int64_t ntiles = (q.capacity + IT - 1) / IT;
+    int64_t grid = (int64_t)ctx->surr_per_sm * ctx->num_sms;
+    if (ntiles < grid) grid = ntiles;
+    InferArgs a{};
+    a.params = m->params;
+    a.flags = ctx->surr_flags ? m->flags : nullptr;
+    a.inv = static_cast<const float *>(ctx->d_nlc_inv);
+    a.n = q.capacity;
+    a.chi = q.chi;
+    a.r = q.r;
+    a.xi = q.xi;
+    a.xi_c = nullptr;
+    a.counters = counters;
+    a.status = nullptr;
+    a.K = kind_of(0);
+    a.n_dev = q.count;
+    ApplyOut &o = a.ap;
+    o.idx = q.index;
+    o.g = q.gamma; o.px = q.px; o.py = q.py; o.pz = q.pz;
+    o.ppx = static_cast<float *>(p->px); o.ppy = static_cast<float *>(p->py); o.ppz = static_cast<float *>(p->pz);
+    o.flags = p->flags;
+    o.id = p->id;
+    o.id_base = p->id_base;
+    o.cap = out->capacity;
+    o.opx = static_cast<float *>(out->px); o.opy = static_cast<float *>(out->py); o.opz = static_cast<float *>(out->pz);
+    o.opid = out->parent_id;
+    o.ostep = out->step;
+    o.ometa = out->meta;
+    o.ocount = out->count;
+    o.step = step;
+    infer_tc_kernel<true><<<(unsigned)grid, IT, INFER_SMEM, stream>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace sfq
 
 // ---------------------------------------------------------------------------------------
@@ -796,6 +959,7 @@ sfq_status sfq_mlp_create_pair(sfq_ctx *ctx, uint64_t seed, sfq_mlp **out) { ret
 
 void sfq_mlp_destroy(sfq_mlp *m) {
     if (!m) return;
+    if (m->ctx->surr == m) m->ctx->surr = nullptr;     // detach from the context's step
     DeviceGuard g(m->ctx->device);
     void *p[6] = {m->params, m->m, m->v, m->grad, m->flags, m->cell_err};
     for (void *q : p)
@@ -958,21 +1122,21 @@ static sfq_status mlp_sample(sfq_mlp *m, int64_t n, const void *chi, const void 
     static bool attr = false;
     cudaError_t e = cudaSuccess;
     if (!attr) {
-        e = cudaFuncSetAttribute(infer_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INFER_SMEM);
+        e = cudaFuncSetAttribute(infer_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INFER_SMEM);
         if (e != cudaSuccess) return cuda_fail(m->ctx, e, "sfq_mlp_sample_photon_xi: attributes");
         attr = true;
     }
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, infer_tc_kernel, IT, INFER_SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, infer_tc_kernel<false>, IT, INFER_SMEM);
     if (e != cudaSuccess || per_sm < 1) per_sm = 1;
-    if (per_sm > 4) per_sm = 4;                    // 4 x 64 tensor-memory columns per SM at most
+    if (per_sm > 8) per_sm = 8;                    // 8 x 64 tensor-memory columns: the SM's 512
     const int64_t ntiles = (n + IT - 1) / IT;
     int64_t grid = (int64_t)per_sm * m->ctx->num_sms;
     if (ntiles < grid) grid = ntiles;
     InferArgs a{m->params, use_flags ? m->flags : nullptr, inv_table(m), n,
                 static_cast<const float *>(chi), static_cast<const float *>(r), static_cast<float *>(xi),
-                static_cast<float *>(xi_c), counters, nullptr, kind_of(m->kind)};
-    infer_tc_kernel<<<(unsigned)grid, IT, INFER_SMEM, (cudaStream_t)stream>>>(a);
+                static_cast<float *>(xi_c), counters, nullptr, kind_of(m->kind), nullptr, ApplyOut{}};
+    infer_tc_kernel<false><<<(unsigned)grid, IT, INFER_SMEM, (cudaStream_t)stream>>>(a);
     e = cudaGetLastError();
     return e == cudaSuccess ? SFQ_OK : cuda_fail(m->ctx, e, "sfq_mlp_sample_*_xi");
 }
@@ -987,6 +1151,43 @@ sfq_status sfq_mlp_sample_pair_xi(sfq_mlp *m, int64_t n, const void *chi, const 
                                   int32_t use_flags, sfq_counters *counters, void *stream) {
     if (m && m->kind != 1) return fail(m->ctx, SFQ_ERR_ARG, "a photon-emission surrogate: use sfq_mlp_sample_photon_xi");
     return mlp_sample(m, n, chi, r, xi_e, xi_p, use_flags, counters, stream);
+}
+
+sfq_status sfq_set_surrogate(sfq_ctx *ctx, sfq_mlp *net, const sfq_event_queue *queue, int32_t use_flags) {
+    if (!ctx) return SFQ_ERR_ARG;
+    if (!net) {
+        ctx->surr = nullptr;
+        ctx->surr_q = sfq_event_queue{};
+        ctx->surr_flags = 0;
+        return SFQ_OK;
+    }
+    if (ctx->cfg.precision != SFQ_FP32) return fail(ctx, SFQ_ERR_ARG, "the surrogate needs a binary32 context");
+    if (net->ctx != ctx) return fail(ctx, SFQ_ERR_ARG, "a surrogate of another context");
+    if (net->kind != 0) return fail(ctx, SFQ_ERR_ARG, "a pair-creation surrogate: the step takes the photon one");
+    if (use_flags && !net->calibrated) return fail(ctx, SFQ_ERR_ARG, "use_flags before sfq_mlp_calibrate");
+    if (ctx->inv_tr > 0) return fail(ctx, SFQ_ERR_ARG, "truncated samplers are set: restore the full coefficients");
+    if (!queue || queue->capacity < 0 || !queue->count || ((uintptr_t)queue->count & 7u))
+        return fail(ctx, SFQ_ERR_ARG, "queue descriptor, capacity or counter invalid");
+    if (queue->capacity > 0) {
+        const void *b[8] = {queue->index, queue->chi, queue->r, queue->gamma, queue->px, queue->py, queue->pz, queue->xi};
+        for (const void *q : b)
+            if (!q || !a16(q)) return fail(ctx, SFQ_ERR_ARG, "queue buffer null or misaligned (16 bytes)");
+    }
+    DeviceGuard g(ctx->device);
+    // kernel attributes and the grid of the surrogate pass, set here (outside any capture)
+    cudaError_t e = sfq::prepare_step_surr_f32();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(infer_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INFER_SMEM);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sfq_set_surrogate: attributes");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, infer_tc_kernel<true>, IT, INFER_SMEM);
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+    if (per_sm > 8) per_sm = 8;                    // 8 x 64 tensor-memory columns: the SM's 512
+    ctx->surr = net;
+    ctx->surr_q = *queue;
+    ctx->surr_flags = use_flags ? 1 : 0;
+    ctx->surr_per_sm = per_sm;
+    return SFQ_OK;
 }
 
 }  // extern "C"

@@ -59,6 +59,13 @@ std::string graph_key(const sfq_ctx *ctx, const sfq_particles *p, const sfq_fiel
     const void *inv_r[3] = {ctx->d_nlc_inv_r, ctx->d_nbw_inv_r, reinterpret_cast<const void *>((intptr_t)ctx->inv_tr)};
     k.append(reinterpret_cast<const char *>(&cut), sizeof(cut));
     k.append(reinterpret_cast<const char *>(inv_r), sizeof(inv_r));
+    // the surrogate on the event path (network, queue, fallback flags)
+    const void *surr = ctx->surr;
+    k.append(reinterpret_cast<const char *>(&surr), sizeof(surr));
+    if (ctx->surr) {
+        k.append(reinterpret_cast<const char *>(&ctx->surr_q), sizeof(ctx->surr_q));
+        k.append(reinterpret_cast<const char *>(&ctx->surr_flags), sizeof(ctx->surr_flags));
+    }
     return k;
 }
 

@@ -61,6 +61,11 @@ struct StepArgs {
     T pair_chi_min;  // NBW rate is zero below this chi (0.01, or the "fast" cutoff)
     Tables<T> tab;
     sfq_counters *counters;
+    // queue of photon emissions for the surrogate pass (the SURR kernel instances only)
+    int64_t qcap;
+    int64_t *qidx;
+    float *qchi, *qr, *qg, *qpx, *qpy, *qpz;
+    unsigned long long *qcount;
 };
 
 // Entry of the TMA-staged kernel's event queue: the particle's state as the step read it,
@@ -337,7 +342,7 @@ __device__ __forceinline__ void reserve_records(unsigned long long *ocount, unsi
 // global atomic per batch, before the sampling when every record count is known up
 // front (no beyond-LCFA lane, whose emission may be rejected), so that the atomic's
 // latency overlaps the sampling.
-template <typename T, bool TRUNC = false, bool CASC = false>
+template <typename T, bool TRUNC = false, bool CASC = false, bool SURR = false>
 __device__ __forceinline__ void process_events_core(const StepArgs<T> &a, uint32_t step, int64_t ei, T eg, T echi,
                                                     T e_aux, T px, T py, T pz, uint8_t fl, bool valid, Cnt &c,
                                                     EvOut<T> &o) {
@@ -345,7 +350,18 @@ __device__ __forceinline__ void process_events_core(const StepArgs<T> &a, uint32
     const bool photon = valid && ((fl >> SFQ_SPECIES_SHIFT) & 3) == SFQ_PHOTON;
     const bool maybe = valid && !photon && !(e_aux < (T)0);        // beyond-LCFA: may be rejected
     const bool late = __any_sync(0xFFFFFFFFu, maybe);
-    int nprod = valid ? (photon ? 2 : 1) : 0;
+    // SURR: photon emissions by the optical-depth method go to the surrogate's queue (one
+    // entry each, reserved warp-wide); an event the queue cannot take is sampled here
+    bool queued = false;
+    unsigned long long qslot = 0;
+    if constexpr (SURR) {
+        const bool want = valid && !photon && e_aux < (T)0;
+        unsigned long long dummy = 0;
+        reserve_records(a.qcount, nullptr, want ? 1 : 0, 0, qslot, dummy);
+        queued = want && qslot < (unsigned long long)a.qcap;
+        c.v[C_SURR] += want && !queued;
+    }
+    int nprod = valid && !queued ? (photon ? 2 : 1) : 0;
     // spawned particles: the pair of a converted photon; in a cascade also the emitted photon
     int nspawn = a.scount ? (photon ? 2 : (CASC ? nprod : 0)) : 0;
     unsigned long long bp = 0, bs = 0;
@@ -365,9 +381,18 @@ __device__ __forceinline__ void process_events_core(const StepArgs<T> &a, uint32
             ++c.v[C_PAIR];
         } else if (e_aux < (T)0) {
             ++c.v[C_EV];
-            xa = photon_s_sel<T, TRUNC>(a.tab, echi, r1, oor);      // s
             xb = uniform<T>(w.w[0]);                               // for the fresh optical depth
-            ++c.v[C_EMIT];
+            if (queued) {
+                // the surrogate pass samples this emission, applies the recoil and writes the record
+                a.qidx[qslot] = ei;
+                a.qchi[qslot] = (float)echi;
+                a.qr[qslot] = (float)r1;
+                a.qg[qslot] = (float)eg;
+                a.qpx[qslot] = (float)px; a.qpy[qslot] = (float)py; a.qpz[qslot] = (float)pz;
+            } else {
+                xa = photon_s_sel<T, TRUNC>(a.tab, echi, r1, oor);  // s
+                ++c.v[C_EMIT];
+            }
         } else {
             // beyond-LCFA: LCFA sample, then the rejection of Eq. rej_cond below gamma_LCFA
             xa = photon_s_sel<T, TRUNC>(a.tab, echi, r1, oor);
@@ -392,6 +417,11 @@ __device__ __forceinline__ void process_events_core(const StepArgs<T> &a, uint32
     }
     if (late) reserve_records(a.ocount, a.scount, nprod, nspawn, bp, bs);
     if (!valid) return;
+    if (queued) {
+        o.tau = to_tau<T>(fresh_tau(xb));                        // fresh optical depth, word 0 (Sec. 2)
+        o.what = 2;
+        return;
+    }
     const T pm = sqrt(fma(px, px, fma(py, py, pz * pz)));
     const T inv_pm = pm > (T)0 ? (T)1 / pm : (T)0;
     const T nx = px * inv_pm, ny = py * inv_pm, nz = pz * inv_pm;
@@ -483,11 +513,11 @@ __device__ __forceinline__ void process_events_core(const StepArgs<T> &a, uint32
 
 // process_events_core at the launch's step with the parent's new state stored to the
 // population in global memory.
-template <typename T, bool TRUNC = false, bool CASC = false>
+template <typename T, bool TRUNC = false, bool CASC = false, bool SURR = false>
 __device__ __forceinline__ void process_events(const StepArgs<T> &a, int64_t ei, T eg, T echi, T e_aux, T px,
                                                T py, T pz, uint8_t fl, bool valid, Cnt &c) {
     EvOut<T> o;
-    process_events_core<T, TRUNC, CASC>(a, a.step, ei, eg, echi, e_aux, px, py, pz, fl, valid, c, o);
+    process_events_core<T, TRUNC, CASC, SURR>(a, a.step, ei, eg, echi, e_aux, px, py, pz, fl, valid, c, o);
     if (o.what & 1) { a.px[ei] = o.px; a.py[ei] = o.py; a.pz[ei] = o.pz; }
     if (o.what & 2) a.tau[ei] = o.tau;
     if (o.what & 4) a.flags[ei] = o.fl;
@@ -597,7 +627,7 @@ __device__ __forceinline__ void step_lepton_pair(const StepArgs<float> &a, const
 // warp-private ring in shared memory; a full batch of 32 events is sampled by the
 // whole warp.  No block-wide barrier inside the loop.
 // CASC: the full-cascade instance (every product is also spawned, with its own id).
-template <typename T, int FK, int PPT, bool TRUNC = false, bool CASC = false>
+template <typename T, int FK, int PPT, bool TRUNC = false, bool CASC = false, bool SURR = false>
 __global__ void __launch_bounds__(STEP_BS, SFQ_STEP_MINB) mc_step_kernel(const StepArgs<T> a) {
     using Q = L<T>;
     constexpr int WARPS = STEP_BS / 32;
@@ -660,7 +690,7 @@ __global__ void __launch_bounds__(STEP_BS, SFQ_STEP_MINB) mc_step_kernel(const S
             const QEntryX<T> e = q[(head + lane) & (QS - 1)];
             __syncwarp();
             head += 32;
-            process_events<T, TRUNC, CASC>(a, e.i, e.g, e.chi, e.aux, a.px[e.i], a.py[e.i], a.pz[e.i], a.flags[e.i], true,
+            process_events<T, TRUNC, CASC, SURR>(a, e.i, e.g, e.chi, e.aux, a.px[e.i], a.py[e.i], a.pz[e.i], a.flags[e.i], true,
                                      c);
         }
     }
@@ -670,7 +700,7 @@ __global__ void __launch_bounds__(STEP_BS, SFQ_STEP_MINB) mc_step_kernel(const S
         const unsigned nv = tail - head;
         const QEntryX<T> e = q[(head + lane) & (QS - 1)];
         const bool v = (unsigned)lane < nv;
-        process_events<T, TRUNC, CASC>(a, e.i, e.g, e.chi, e.aux, v ? a.px[e.i] : (T)0, v ? a.py[e.i] : (T)0,
+        process_events<T, TRUNC, CASC, SURR>(a, e.i, e.g, e.chi, e.aux, v ? a.px[e.i] : (T)0, v ? a.py[e.i] : (T)0,
                           v ? a.pz[e.i] : (T)0, v ? a.flags[e.i] : (uint8_t)0, v, c);
     }
     flush_counters(c, a.counters);

@@ -108,7 +108,7 @@ __global__ void wait_check_kernel(uint32_t polls, sfq_counters *c) {
     }
 }
 
-template <typename T, int FK, int CW, bool TRUNC = false>
+template <typename T, int FK, int CW, bool TRUNC = false, bool SURR = false>
 __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const StepArgs<T> a) {
     using Q = L<T>;
     using S = TmaStage<T, FK, CW>;
@@ -386,24 +386,24 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
             const QEntry<T> e = q[(head + lane) & (QS - 1)];
             __syncwarp();
             head += 32;
-            process_events<T, TRUNC>(a, e.i, e.g, e.chi, (T)-1, e.px, e.py, e.pz, (uint8_t)e.fl, true, c);
+            process_events<T, TRUNC, false, SURR>(a, e.i, e.g, e.chi, (T)-1, e.px, e.py, e.pz, (uint8_t)e.fl, true, c);
         }
     }
     __syncwarp();
     if (tail != head) {
         const unsigned nv = tail - head;
         const QEntry<T> e = q[(head + lane) & (QS - 1)];
-        process_events<T, TRUNC>(a, e.i, e.g, e.chi, (T)-1, e.px, e.py, e.pz, (uint8_t)e.fl, (unsigned)lane < nv,
+        process_events<T, TRUNC, false, SURR>(a, e.i, e.g, e.chi, (T)-1, e.px, e.py, e.pz, (uint8_t)e.fl, (unsigned)lane < nv,
                                  c);
     }
     // counters of the consumer warps (the producer warp has returned)
     if (a.counters) {
 #pragma unroll
-        for (int k = 0; k < 12; ++k) {
+        for (int k = 0; k < (SURR ? 13 : 12); ++k) {
             unsigned long long v = (unsigned long long)c.v[k];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
-            if (lane == 0 && v) atomicAdd(reinterpret_cast<unsigned long long *>(a.counters) + k, v);
+            if (lane == 0 && v) atomicAdd(reinterpret_cast<unsigned long long *>(a.counters) + (k < 12 ? k : 13), v);
         }
     }
 }

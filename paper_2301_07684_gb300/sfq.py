@@ -59,6 +59,12 @@ class Spawn(C.Structure):
     _fields_ = [("p", Particles), ("k0", C.c_void_p), ("amp", C.c_void_p), ("count", C.c_void_p)]
 
 
+class EventQueueDesc(C.Structure):
+    _fields_ = [("capacity", C.c_int64), ("index", C.c_void_p), ("chi", C.c_void_p), ("r", C.c_void_p),
+                ("gamma", C.c_void_p), ("px", C.c_void_p), ("py", C.c_void_p), ("pz", C.c_void_p),
+                ("xi", C.c_void_p), ("count", C.c_void_p)]
+
+
 _lib = None
 
 
@@ -149,6 +155,8 @@ def lib():
         L.sfq_table_pieces.restype = st
         L.sfq_set_step_shape.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
         L.sfq_set_step_shape.restype = st
+        L.sfq_set_surrogate.argtypes = [vp, vp, C.POINTER(EventQueueDesc), C.c_int32]
+        L.sfq_set_surrogate.restype = st
         L.sfq_counters_check.argtypes = [vp]
         L.sfq_counters_check.restype = st
         L.sfq_check_bounded_wait.argtypes = [vp, u32, vp, vp]
@@ -166,7 +174,7 @@ EXPORTED = ["sfq_init", "sfq_finalize", "sfq_last_error", "sfq_constants", "sfq_
             "sfq_mlp_loss_grad", "sfq_mlp_train", "sfq_mlp_predict_lnw", "sfq_mlp_plain_targets", "sfq_mlp_calibrate",
             "sfq_mlp_sample_photon_xi", "sfq_mlp_create_pair", "sfq_mlp_sample_pair_xi",
             "sfq_cascade_run", "sfq_cascade_compact_scratch_bytes", "sfq_cascade_compact", "sfq_set_evaluator",
-            "sfq_table_pieces", "sfq_counters_check", "sfq_check_bounded_wait",
+            "sfq_table_pieces", "sfq_counters_check", "sfq_check_bounded_wait", "sfq_set_surrogate",
             "sfq_version"]
 
 
@@ -376,6 +384,17 @@ class Context:
         self._check(lib().sfq_sort_products_noalloc(self._h, C.byref(O), n, _stream()),
                     "sfq_sort_products_noalloc")
 
+    def set_surrogate(self, net, queue=None, use_flags=True):
+        """sfq_set_surrogate: photon emissions of the step drawn from `net` (a calibrated photon
+        Surrogate of this context) through `queue` (an EventQueue); net=None detaches."""
+        if net is None:
+            self._check(lib().sfq_set_surrogate(self._h, None, None, 0), "sfq_set_surrogate")
+            self._surrogate = None
+            return
+        D = queue.descriptor()
+        self._check(lib().sfq_set_surrogate(self._h, net._h, C.byref(D), int(bool(use_flags))), "sfq_set_surrogate")
+        self._surrogate = (net, queue)          # keep both alive while attached
+
     def check_bounded_wait(self, polls, counters):
         """sfq_check_bounded_wait: a wait that nothing completes gives up after `polls` polls
         and adds 1 to counters' timeouts word (counters: a device counters_tensor)."""
@@ -385,6 +404,29 @@ class Context:
 
 SORT_NOALLOC_MAX_N = 1 << 20
 SORT_NOALLOC_SCRATCH_BYTES = 44 << 20
+
+
+class EventQueue:
+    """Caller-owned queue of a step's photon emissions for the surrogate pass (sfq_event_queue)."""
+
+    def __init__(self, capacity, device="cuda"):
+        self.capacity = int(capacity)
+        pad = max(self.capacity, 1)
+        f = lambda: torch.empty(pad, dtype=torch.float32, device=device)
+        self.index = torch.empty(pad, dtype=torch.int64, device=device)
+        self.chi, self.r, self.gamma, self.px, self.py, self.pz, self.xi = (f() for _ in range(7))
+        self.count = torch.zeros(2, dtype=torch.int64, device=device)
+
+    def n(self):
+        return min(int(self.count[0].item()), self.capacity)
+
+    def descriptor(self):
+        D = EventQueueDesc()
+        D.capacity = self.capacity
+        D.index, D.chi, D.r, D.gamma = _ptr(self.index), _ptr(self.chi), _ptr(self.r), _ptr(self.gamma)
+        D.px, D.py, D.pz, D.xi = _ptr(self.px), _ptr(self.py), _ptr(self.pz), _ptr(self.xi)
+        D.count = _ptr(self.count)
+        return D
 
 
 class Surrogate:

@@ -32,3 +32,13 @@ def oracle():
     from oracle import oracle as O
     O.build()
     return O
+
+
+@pytest.fixture(scope="session")
+def dense_photon_cdf():
+    """The oracle's dense FP64 CDF of the photon energy fraction (Eq. pe_eff_int_2), built once
+    per session for the surrogate tests (about a minute of CPU)."""
+    from oracle import oracle as O
+    O.build()
+    from oracle import surrogate as S
+    return S.DenseCDF()

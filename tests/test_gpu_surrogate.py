@@ -26,11 +26,9 @@ CHI_LO, CHI_HI = 1e-3, 100.0
 
 
 @pytest.fixture(scope="module")
-def dense():
+def dense(dense_photon_cdf):
     from oracle import oracle as O
-    O.build()
-    from oracle import surrogate as S
-    T = S.DenseCDF()
+    T = dense_photon_cdf
     # the fine table against direct quadrature at a few off-grid points
     g = np.random.default_rng(11)
     chi = np.exp(g.uniform(np.log(CHI_LO), np.log(CHI_HI), 24))
