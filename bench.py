@@ -843,7 +843,7 @@ def run_ours(args):
         replay = None
         if main["final"] is not None:
             replay = dict(d=d, final=main["final"], warmup=args.warmup, steps=args.steps, seed=12345)
-        cpu = cpu_baseline(args, replay) if world == 1 else None
+        cpu = cpu_baseline(args, replay) if world == 1 and args.oracle_particles > 0 else None
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         dev_name = torch.cuda.get_device_name(local)
         line = {
