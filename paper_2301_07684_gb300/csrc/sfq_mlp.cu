@@ -915,6 +915,18 @@ struct DeviceGuard {
 };
 bool a16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
+// Attributes of an inference kernel instance: its dynamic shared memory, and the largest
+// shared-memory carveout, so that INFER_MINB blocks (4 x 40 KB) are resident on an SM.  The
+// grid is then INFER_MINB blocks per SM: registers (at most 128 a thread by the launch
+// bounds), shared memory and tensor memory (4 x 64 of the 512 columns) all admit them.
+template <typename K>
+cudaError_t set_infer_attributes(K kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INFER_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
 // The plain fitted sampler the surrogate stands for (training targets, calibration, fallback).
 const float *inv_table(const sfq_mlp *m) {
     return static_cast<const float *>(m->kind ? m->ctx->d_nbw_inv : m->ctx->d_nlc_inv);
@@ -1122,14 +1134,11 @@ static sfq_status mlp_sample(sfq_mlp *m, int64_t n, const void *chi, const void 
     static bool attr = false;
     cudaError_t e = cudaSuccess;
     if (!attr) {
-        e = cudaFuncSetAttribute(infer_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INFER_SMEM);
+        e = set_infer_attributes(infer_tc_kernel<false>);
         if (e != cudaSuccess) return cuda_fail(m->ctx, e, "sfq_mlp_sample_photon_xi: attributes");
         attr = true;
     }
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, infer_tc_kernel<false>, IT, INFER_SMEM);
-    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
-    if (per_sm > 8) per_sm = 8;                    // 8 x 64 tensor-memory columns: the SM's 512
+    const int per_sm = INFER_MINB;
     const int64_t ntiles = (n + IT - 1) / IT;
     int64_t grid = (int64_t)per_sm * m->ctx->num_sms;
     if (ntiles < grid) grid = ntiles;
@@ -1176,13 +1185,9 @@ sfq_status sfq_set_surrogate(sfq_ctx *ctx, sfq_mlp *net, const sfq_event_queue *
     DeviceGuard g(ctx->device);
     // kernel attributes and the grid of the surrogate pass, set here (outside any capture)
     cudaError_t e = sfq::prepare_step_surr_f32();
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(infer_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INFER_SMEM);
+    if (e == cudaSuccess) e = set_infer_attributes(infer_tc_kernel<true>);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sfq_set_surrogate: attributes");
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, infer_tc_kernel<true>, IT, INFER_SMEM);
-    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
-    if (per_sm > 8) per_sm = 8;                    // 8 x 64 tensor-memory columns: the SM's 512
+    const int per_sm = INFER_MINB;
     ctx->surr = net;
     ctx->surr_q = *queue;
     ctx->surr_flags = use_flags ? 1 : 0;

@@ -627,8 +627,11 @@ __device__ __forceinline__ void step_lepton_pair(const StepArgs<float> &a, const
 // warp-private ring in shared memory; a full batch of 32 events is sampled by the
 // whole warp.  No block-wide barrier inside the loop.
 // CASC: the full-cascade instance (every product is also spawned, with its own id).
-template <typename T, int FK, int PPT, bool TRUNC = false, bool CASC = false, bool SURR = false>
-__global__ void __launch_bounds__(STEP_BS, SFQ_STEP_MINB) mc_step_kernel(const StepArgs<T> a) {
+// MINB: resident blocks per SM the register allocation aims for (the beyond-LCFA lepton
+// instance takes 2: its event path holds the force history and the rejection's spectra).
+template <typename T, int FK, int PPT, bool TRUNC = false, bool CASC = false, bool SURR = false,
+          int MINB = SFQ_STEP_MINB>
+__global__ void __launch_bounds__(STEP_BS, MINB) mc_step_kernel(const StepArgs<T> a) {
     using Q = L<T>;
     constexpr int WARPS = STEP_BS / 32;
     constexpr int QS = (32 * (PPT + 1) <= 64) ? 64 : ((32 * (PPT + 1) <= 128) ? 128 : 256);
