@@ -221,14 +221,14 @@ static cudaError_t launch_step_t(const StepLaunch &L) {
     }
     void (*kern)(const StepArgs<T>) = nullptr;
     if (L.cascade) {
-        // the full cascade (plane-wave fields only) runs its own instance of this kernel, with
-        // the looser register bound (its event path also spawns every product)
-        kern = mc_step_kernel<T, FK_PW, TRUNC ? TRUNC_PPT : 2, TRUNC, true, false, 2>;
+        // the full cascade (plane-wave fields only) runs its own instance of this kernel
+        kern = mc_step_kernel<T, FK_PW, TRUNC ? TRUNC_PPT : 2, TRUNC, true, false, SFQ_LEPTON_MINB>;
     } else if constexpr (TRUNC) {
         kern = pw ? mc_step_kernel<T, FK_PW, TRUNC_PPT, true> : mc_step_kernel<T, FK_SOA, TRUNC_PPT, true>;
     } else if (p.lepton_model != SFQ_LEPTON_LCFA_OD) {
-        // beyond-LCFA leptons: their own instance with the looser register bound
-        kern = pw ? mc_step_kernel<T, FK_PW, 2, false, false, false, 2> : mc_step_kernel<T, FK_SOA, 2, false, false, false, 2>;
+        // beyond-LCFA leptons: their own instance
+        kern = pw ? mc_step_kernel<T, FK_PW, 2, false, false, false, SFQ_LEPTON_MINB>
+                 : mc_step_kernel<T, FK_SOA, 2, false, false, false, SFQ_LEPTON_MINB>;
     } else {
         switch ((pw ? 10 : 0) + L.ppt) {
             case 1: kern = mc_step_kernel<T, FK_SOA, 1>; break;

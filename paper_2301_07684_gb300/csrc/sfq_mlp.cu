@@ -581,7 +581,10 @@ constexpr uint32_t SM_A = 0, SM_B2 = 16384, SM_B3 = 24576, SM_SMALL = 32768;
 constexpr uint32_t SM_FLAGS = SM_SMALL + (H * 2 + 4 * H + 4) * 4;
 constexpr uint32_t SM_BYTES = SM_FLAGS + NCELL;
 constexpr uint32_t INFER_SMEM = SM_BYTES + 1024;     // + alignment slack
-constexpr int INFER_MINB = 4;                         // resident blocks per SM the registers allow
+#ifndef SFQ_INFER_MINB
+#define SFQ_INFER_MINB 5
+#endif
+constexpr int INFER_MINB = SFQ_INFER_MINB;            // resident blocks per SM (registers, 40 KB of shared memory each)
 
 // Eight bfloat16 (one 16-byte K chunk of an operand row) from eight binary32 values.
 __device__ __forceinline__ uint4 pack8_bf16(const float *a) {
@@ -916,9 +919,9 @@ struct DeviceGuard {
 bool a16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 // Attributes of an inference kernel instance: its dynamic shared memory, and the largest
-// shared-memory carveout, so that INFER_MINB blocks (4 x 40 KB) are resident on an SM.  The
-// grid is then INFER_MINB blocks per SM: registers (at most 128 a thread by the launch
-// bounds), shared memory and tensor memory (4 x 64 of the 512 columns) all admit them.
+// shared-memory carveout, so that INFER_MINB blocks (5 x 40 KB) are resident on an SM.  The
+// grid is then INFER_MINB blocks per SM: registers (at most 102 a thread by the launch
+// bounds), shared memory and tensor memory (5 x 64 of the 512 columns) all admit them.
 template <typename K>
 cudaError_t set_infer_attributes(K kern) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INFER_SMEM);

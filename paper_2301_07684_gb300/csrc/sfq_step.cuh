@@ -97,6 +97,9 @@ constexpr int STEP_BS = 256;
 #ifndef SFQ_STEP_MINB
 #define SFQ_STEP_MINB 4   // resident blocks per SM the register allocation aims for (measured best)
 #endif
+#ifndef SFQ_LEPTON_MINB
+#define SFQ_LEPTON_MINB 4 // the same for the beyond-LCFA lepton and full-cascade instances
+#endif
 
 enum { FK_SOA = 0, FK_PW = 1 };
 
@@ -627,8 +630,8 @@ __device__ __forceinline__ void step_lepton_pair(const StepArgs<float> &a, const
 // warp-private ring in shared memory; a full batch of 32 events is sampled by the
 // whole warp.  No block-wide barrier inside the loop.
 // CASC: the full-cascade instance (every product is also spawned, with its own id).
-// MINB: resident blocks per SM the register allocation aims for (the beyond-LCFA lepton
-// instance takes 2: its event path holds the force history and the rejection's spectra).
+// MINB: resident blocks per SM the register allocation aims for (the beyond-LCFA lepton and
+// full-cascade instances take SFQ_LEPTON_MINB: their event paths hold more state).
 template <typename T, int FK, int PPT, bool TRUNC = false, bool CASC = false, bool SURR = false,
           int MINB = SFQ_STEP_MINB>
 __global__ void __launch_bounds__(STEP_BS, MINB) mc_step_kernel(const StepArgs<T> a) {
