@@ -579,12 +579,12 @@ __device__ __forceinline__ unsigned long long warp_reserve(unsigned long long *c
 
 constexpr uint32_t SM_A = 0, SM_B2 = 16384, SM_B3 = 24576, SM_SMALL = 32768;
 constexpr uint32_t SM_FLAGS = SM_SMALL + (H * 2 + 4 * H + 4) * 4;
-constexpr uint32_t SM_BYTES = SM_FLAGS + NCELL;
+constexpr uint32_t SM_BYTES = SM_FLAGS + NCELL / 8;    // the fallback flags as one bit per cell
 constexpr uint32_t INFER_SMEM = SM_BYTES + 1024;     // + alignment slack
 #ifndef SFQ_INFER_MINB
-#define SFQ_INFER_MINB 5
+#define SFQ_INFER_MINB 6
 #endif
-constexpr int INFER_MINB = SFQ_INFER_MINB;            // resident blocks per SM (registers, 40 KB of shared memory each)
+constexpr int INFER_MINB = SFQ_INFER_MINB;            // resident blocks per SM (registers, 36 KB of shared memory each)
 
 // Eight bfloat16 (one 16-byte K chunk of an operand row) from eight binary32 values.
 __device__ __forceinline__ uint4 pack8_bf16(const float *a) {
@@ -642,7 +642,7 @@ __global__ void __launch_bounds__(IT, INFER_MINB) infer_tc_kernel(const InferArg
     const uint32_t sbase = s_u32(sm);
     float *w1 = reinterpret_cast<float *>(sm + SM_SMALL);
     float *b1 = w1 + 2 * H, *hb2 = b1 + H, *hb3 = hb2 + H, *w4 = hb3 + H, *b4 = w4 + H;
-    uint8_t *fl = sm + SM_FLAGS;
+    uint32_t *fl = reinterpret_cast<uint32_t *>(sm + SM_FLAGS);
     const int tid = threadIdx.x, warp = tid >> 5;
     const float *P = a.params;
 
@@ -655,15 +655,21 @@ __global__ void __launch_bounds__(IT, INFER_MINB) infer_tc_kernel(const InferArg
         *reinterpret_cast<__nv_bfloat16 *>(sm + SM_B3 + off) = __float2bfloat16_rn(P[O_W3 + e]);
     }
     for (int e = tid; e < H; e += IT) {
-        w1[2 * e] = bf16r(P[O_W1 + 2 * e]);
-        w1[2 * e + 1] = bf16r(P[O_W1 + 2 * e + 1]);
-        b1[e] = P[O_B1 + e];
+        // layer 1 halved as well (exact: a power of two), so that h = z / 2 comes out of its fmas
+        w1[2 * e] = 0.5f * bf16r(P[O_W1 + 2 * e]);
+        w1[2 * e + 1] = 0.5f * bf16r(P[O_W1 + 2 * e + 1]);
+        b1[e] = 0.5f * P[O_B1 + e];
         hb2[e] = 0.5f * P[O_B2 + e];
         hb3[e] = 0.5f * P[O_B3 + e];
         w4[e] = bf16r(P[O_W4 + e]);
     }
     if (tid == 0) *b4 = P[O_B4];
-    for (int e = tid; e < NCELL; e += IT) fl[e] = a.flags ? a.flags[e] : 0;
+    for (int e = tid; e < NCELL / 32; e += IT) {
+        uint32_t w = 0;
+        if (a.flags)
+            for (int b = 0; b < 32; ++b) w |= (a.flags[32 * e + b] ? 1u : 0u) << b;
+        fl[e] = w;
+    }
     if (tid < 6) s_cnt[tid] = 0;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_u32(&tmem_base)),
@@ -700,7 +706,8 @@ __global__ void __launch_bounds__(IT, INFER_MINB) infer_tc_kernel(const InferArg
         const float rp = 2.0f * r - 1.0f;                 // pair creation: r' (exact for r in (0, 1))
         const float u = a.K.pair ? fabsf(rp) : r;
         const bool in_range = chi >= a.K.chi_lo && chi <= a.K.chi_hi;
-        const bool fallback = !bad && (!in_range || fl[cell_of(a.K, chi, u)]);
+        const int cell = cell_of(a.K, chi, u);
+        const bool fallback = !bad && (!in_range || ((fl[cell >> 5] >> (cell & 31)) & 1u));
         // layer 1 on the CUDA cores (binary32 features, bf16-rounded weights), 8 columns at a time
         float x1, x2;
         features(a.K, in_range ? chi : 1.0f, bad ? 0.5f : u, x1, x2);
@@ -710,7 +717,7 @@ __global__ void __launch_bounds__(IT, INFER_MINB) infer_tc_kernel(const InferArg
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int j = 8 * c + q;
-                v[q] = silu_h(0.5f * fmaf(w1[2 * j], x1, fmaf(w1[2 * j + 1], x2, b1[j])));
+                v[q] = silu_h(fmaf(w1[2 * j], x1, fmaf(w1[2 * j + 1], x2, b1[j])));
             }
             *reinterpret_cast<uint4 *>(sm + SM_A + row_chunk_offset(tid, c)) = pack8_bf16(v);
         }
@@ -919,9 +926,9 @@ struct DeviceGuard {
 bool a16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 // Attributes of an inference kernel instance: its dynamic shared memory, and the largest
-// shared-memory carveout, so that INFER_MINB blocks (5 x 40 KB) are resident on an SM.  The
-// grid is then INFER_MINB blocks per SM: registers (at most 102 a thread by the launch
-// bounds), shared memory and tensor memory (5 x 64 of the 512 columns) all admit them.
+// shared-memory carveout, so that INFER_MINB blocks (6 x 36 KB) are resident on an SM.  The
+// grid is then INFER_MINB blocks per SM: registers (at most 85 a thread by the launch
+// bounds), shared memory and tensor memory (6 x 64 of the 512 columns) all admit them.
 template <typename K>
 cudaError_t set_infer_attributes(K kern) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INFER_SMEM);
