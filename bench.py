@@ -218,6 +218,10 @@ def run_ours(args):
             ctx.set_sampler_coefficients(sampler_k)
         P = make_state(sfq, torch, d, dtype, device)
         P.id_base = rank * n
+        if args.event_pass and precision == "fp32" and not sampler_k:
+            # the deferred event path: the step kernel queues the emissions, an event pass
+            # samples and finishes them (identical results to the inline path)
+            ctx.set_event_queue(sfq.EventQueue(int(0.12 * n) + 1024, device))
         nslab = steps + warmup
         out = sfq.ProductBuffers(int(0.09 * n * (steps + 1)) + 4096, dtype, device)
         cnt = sfq.counters_tensor(device)
@@ -852,6 +856,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32 (f64 optical depth)", "data": "synthetic",
             "config": {"workload": WORKLOAD, "particles": n, "fields": "SoA, distinct slab per step",
                        "precision": "fp32-mixed", "l2": "inputs larger than L2 (~760 MB read per step)",
+                       "event_path": "deferred (step kernel, then an event pass)" if args.event_pass else "inline",
                        "launch_shape": main["shape"],
                        "parallelism": f"dp{world} (independent particles, no collective)"},
             "roofline": {"bound": "hbm", "achieved": main["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
@@ -1074,6 +1079,8 @@ def main():
     ap.add_argument("--oracle-config1", type=int, default=1, help="also time the oracle on config 1 (0: skip)")
     ap.add_argument("--oracle-particles", type=int, default=512,
                     help="sampled particles of the timed run the oracle replays (CPU baseline and parity sample)")
+    ap.add_argument("--event-pass", type=int, default=1,
+                    help="binary32 per-step legs run the deferred event path (0: the inline event path)")
     ap.add_argument("--repeats", type=int, default=10,
                     help="timed regions of --steps steps each (at least); the line reports the median")
     ap.add_argument("--min-timed-ms", type=float, default=1500.0,

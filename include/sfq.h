@@ -499,6 +499,20 @@ typedef struct {
  * surrogate, a net of another context, or NULL/misaligned queue buffers. */
 sfq_status sfq_set_surrogate(sfq_ctx *ctx, sfq_mlp *net, const sfq_event_queue *queue, int32_t use_flags);
 
+/* The deferred event path with the plain fitted sampler (no counterpart in the paper: a
+ * launch structure).  With a queue set (binary32 context), every sfq_mc_step and sfq_mc_run
+ * of the context runs photon emission by the optical-depth method in two launches: the
+ * step kernel streams the population, decides the events (Sec. 2) and appends each
+ * emission to the queue; an event pass samples the queued emissions (Eq. again with the
+ * fitted tables, as sfq_sample_photon_xi), recoils each emitter and appends the photon's
+ * record (Sec. 3).  The arithmetic is the inline path's, so the records (in another order),
+ * the state and the counters equal those of the step without a queue.  Emissions past
+ * the capacity are finished inline by the step kernel (counted in surrogate_fallbacks).
+ * The queue's xi column is not written.  A surrogate attached with sfq_set_surrogate takes
+ * precedence.  queue == NULL restores the inline path.  SFQ_ERR_ARG for a binary64 context,
+ * truncated samplers, or NULL/misaligned queue buffers. */
+sfq_status sfq_set_event_queue(sfq_ctx *ctx, const sfq_event_queue *queue);
+
 /* Launch shape of sfq_mc_step for this context, the knob the autotuner turns.
  *   variant: 0 = automatic; 1 = warp-streaming kernel (each warp loads its particles
  *            directly); 2 = TMA-staged kernel (bulk copies of each tile into shared

@@ -114,11 +114,15 @@ cudaError_t launch_step(const sfq_ctx *ctx, const sfq_particles *p, const sfq_fi
     if (p->n == 0) return cudaSuccess;
     const int ppt = ctx->step_ppt ? ctx->step_ppt : (ctx->cfg.precision == SFQ_FP64 ? 1 : 2);
     StepLaunch L{ctx, p, f, step, out, spawn, counters, stream, ctx->step_grid, ppt, ctx->step_variant, cascade};
-    if (ctx->surr && !cascade && ctx->cfg.precision == SFQ_FP32 && p->lepton_model == SFQ_LEPTON_LCFA_OD) {
-        // photon emissions through the surrogate: queue them, then sample and finish them
-        cudaError_t e = cudaMemsetAsync(ctx->surr_q.count, 0, sizeof(unsigned long long), stream);
+    if ((ctx->surr || ctx->defer_q.count) && !cascade && ctx->cfg.precision == SFQ_FP32 &&
+        p->lepton_model == SFQ_LEPTON_LCFA_OD) {
+        // photon emissions deferred to a queue, then sampled and finished in a pass of their
+        // own: by the surrogate (sfq_set_surrogate) or by the plain sampler (sfq_set_event_queue)
+        const sfq_event_queue &q = ctx->surr ? ctx->surr_q : ctx->defer_q;
+        cudaError_t e = cudaMemsetAsync(q.count, 0, sizeof(unsigned long long), stream);
         if (e == cudaSuccess) e = launch_step_surr_f32(L);
-        if (e == cudaSuccess) e = launch_surrogate_apply(ctx, p, step, out, counters, stream);
+        if (e == cudaSuccess)
+            e = ctx->surr ? launch_surrogate_apply(ctx, p, step, out, counters, stream) : launch_event_pass_f32(L);
         return e;
     }
     return ctx->cfg.precision == SFQ_FP64 ? launch_step_f64(L) : launch_step_f32(L);
@@ -469,7 +473,8 @@ sfq_status sfq_set_sampler_coefficients(sfq_ctx *ctx, int32_t k) {
     if (!ctx) return SFQ_ERR_ARG;
     const int n = sfq::inv_coefficients(ctx->cfg.precision);
     if (k < n - 2 || k > n) return fail(ctx, SFQ_ERR_ARG, "coefficients per variable must be n, n - 1 or n - 2");
-    if (k < n && ctx->surr) return fail(ctx, SFQ_ERR_ARG, "truncated samplers with a surrogate attached");
+    if (k < n && (ctx->surr || ctx->defer_q.count))
+        return fail(ctx, SFQ_ERR_ARG, "truncated samplers with a deferred event path or a surrogate attached");
     if (k < n && ctx->eval == SFQ_EVAL_CLENSHAW)
         return fail(ctx, SFQ_ERR_ARG, "truncated samplers need the Horner evaluator");
     const int tr = n - k;
@@ -516,6 +521,28 @@ sfq_status sfq_set_step_shape(sfq_ctx *ctx, int32_t variant, int32_t ppt, int32_
     ctx->step_variant = variant;
     ctx->step_ppt = ppt;
     ctx->step_grid = grid_blocks;
+    return SFQ_OK;
+}
+
+sfq_status sfq_set_event_queue(sfq_ctx *ctx, const sfq_event_queue *queue) {
+    if (!ctx) return SFQ_ERR_ARG;
+    if (!queue) {
+        ctx->defer_q = sfq_event_queue{};
+        return SFQ_OK;
+    }
+    if (ctx->cfg.precision != SFQ_FP32) return fail(ctx, SFQ_ERR_ARG, "the deferred event path needs a binary32 context");
+    if (ctx->inv_tr > 0) return fail(ctx, SFQ_ERR_ARG, "truncated samplers are set: restore the full coefficients");
+    if (queue->capacity < 0 || !queue->count || !aligned8(queue->count))
+        return fail(ctx, SFQ_ERR_ARG, "queue capacity or counter invalid");
+    if (queue->capacity > 0) {
+        const void *b[7] = {queue->index, queue->chi, queue->r, queue->gamma, queue->px, queue->py, queue->pz};
+        for (const void *q : b)
+            if (!q || !aligned16(q)) return fail(ctx, SFQ_ERR_ARG, "queue buffer null or misaligned (16 bytes)");
+    }
+    DeviceGuard g(ctx->device);
+    const cudaError_t e = sfq::prepare_step_surr_f32();    // kernel attributes, outside any capture
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sfq_set_event_queue: attributes");
+    ctx->defer_q = *queue;
     return SFQ_OK;
 }
 

@@ -32,6 +32,8 @@ struct sfq_ctx {
     sfq_event_queue surr_q{};
     int surr_flags = 0;
     int surr_per_sm = 1;
+    // the deferred event path with the plain sampler (sfq_set_event_queue)
+    sfq_event_queue defer_q{};
     std::string err;
 };
 
@@ -93,6 +95,7 @@ cudaError_t launch_step_trunc_f32(const StepLaunch &);
 // and the surrogate pass that samples and finishes them (sfq_mlp.cu).
 cudaError_t launch_step_surr_f32(const StepLaunch &);
 cudaError_t prepare_step_surr_f32();
+cudaError_t launch_event_pass_f32(const StepLaunch &);
 cudaError_t launch_surrogate_apply(const sfq_ctx *ctx, const sfq_particles *p, uint32_t step, const sfq_products *out,
                                    sfq_counters *counters, cudaStream_t stream);
 cudaError_t launch_step_trunc_f64(const StepLaunch &);

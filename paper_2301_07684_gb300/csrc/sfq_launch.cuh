@@ -162,8 +162,8 @@ static StepArgs<T> make_step_args(const StepLaunch &L) {
     a.pair_chi_min = (T)ctx->pair_chi_min;
     a.tab = tables_of<T>(ctx);
     a.counters = L.counters;
-    if (ctx->surr) {
-        const sfq_event_queue &q = ctx->surr_q;
+    if (ctx->surr || ctx->defer_q.count) {
+        const sfq_event_queue &q = ctx->surr ? ctx->surr_q : ctx->defer_q;
         a.qcap = q.capacity;
         a.qidx = q.index;
         a.qchi = q.chi; a.qr = q.r; a.qg = q.gamma;

@@ -66,6 +66,7 @@ std::string graph_key(const sfq_ctx *ctx, const sfq_particles *p, const sfq_fiel
         k.append(reinterpret_cast<const char *>(&ctx->surr_q), sizeof(ctx->surr_q));
         k.append(reinterpret_cast<const char *>(&ctx->surr_flags), sizeof(ctx->surr_flags));
     }
+    k.append(reinterpret_cast<const char *>(&ctx->defer_q), sizeof(ctx->defer_q));   // the deferred event path
     return k;
 }
 

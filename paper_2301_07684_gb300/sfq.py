@@ -155,6 +155,8 @@ def lib():
         L.sfq_table_pieces.restype = st
         L.sfq_set_step_shape.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
         L.sfq_set_step_shape.restype = st
+        L.sfq_set_event_queue.argtypes = [vp, C.POINTER(EventQueueDesc)]
+        L.sfq_set_event_queue.restype = st
         L.sfq_set_surrogate.argtypes = [vp, vp, C.POINTER(EventQueueDesc), C.c_int32]
         L.sfq_set_surrogate.restype = st
         L.sfq_counters_check.argtypes = [vp]
@@ -175,6 +177,7 @@ EXPORTED = ["sfq_init", "sfq_finalize", "sfq_last_error", "sfq_constants", "sfq_
             "sfq_mlp_sample_photon_xi", "sfq_mlp_create_pair", "sfq_mlp_sample_pair_xi",
             "sfq_cascade_run", "sfq_cascade_compact_scratch_bytes", "sfq_cascade_compact", "sfq_set_evaluator",
             "sfq_table_pieces", "sfq_counters_check", "sfq_check_bounded_wait", "sfq_set_surrogate",
+            "sfq_set_event_queue",
             "sfq_version"]
 
 
@@ -394,6 +397,17 @@ class Context:
         D = queue.descriptor()
         self._check(lib().sfq_set_surrogate(self._h, net._h, C.byref(D), int(bool(use_flags))), "sfq_set_surrogate")
         self._surrogate = (net, queue)          # keep both alive while attached
+
+    def set_event_queue(self, queue=None):
+        """sfq_set_event_queue: the deferred event path (step kernel, then an event pass) with
+        `queue` (an EventQueue); None restores the inline path."""
+        if queue is None:
+            self._check(lib().sfq_set_event_queue(self._h, None), "sfq_set_event_queue")
+            self._event_queue = None
+            return
+        D = queue.descriptor()
+        self._check(lib().sfq_set_event_queue(self._h, C.byref(D)), "sfq_set_event_queue")
+        self._event_queue = queue
 
     def check_bounded_wait(self, polls, counters):
         """sfq_check_bounded_wait: a wait that nothing completes gives up after `polls` polls
