@@ -1079,8 +1079,9 @@ def main():
     ap.add_argument("--oracle-config1", type=int, default=1, help="also time the oracle on config 1 (0: skip)")
     ap.add_argument("--oracle-particles", type=int, default=512,
                     help="sampled particles of the timed run the oracle replays (CPU baseline and parity sample)")
-    ap.add_argument("--event-pass", type=int, default=1,
-                    help="binary32 per-step legs run the deferred event path (0: the inline event path)")
+    ap.add_argument("--event-pass", type=int, default=0,
+                    help="1: binary32 per-step legs run the deferred event path (measured slower on GB300: "
+                         "0.229 against 0.200 ms per 2^24 step)")
     ap.add_argument("--repeats", type=int, default=10,
                     help="timed regions of --steps steps each (at least); the line reports the median")
     ap.add_argument("--min-timed-ms", type=float, default=1500.0,

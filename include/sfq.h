@@ -509,7 +509,8 @@ sfq_status sfq_set_surrogate(sfq_ctx *ctx, sfq_mlp *net, const sfq_event_queue *
  * the state and the counters equal those of the step without a queue.  Emissions past
  * the capacity are finished inline by the step kernel (counted in surrogate_fallbacks).
  * The queue's xi column is not written.  A surrogate attached with sfq_set_surrogate takes
- * precedence.  queue == NULL restores the inline path.  SFQ_ERR_ARG for a binary64 context,
+ * precedence.  On GB300 the inline path is the faster one for dense populations (the event
+ * pass gathers each sample's coefficients without the stream to hide them behind).  queue == NULL restores the inline path.  SFQ_ERR_ARG for a binary64 context,
  * truncated samplers, or NULL/misaligned queue buffers. */
 sfq_status sfq_set_event_queue(sfq_ctx *ctx, const sfq_event_queue *queue);
 
