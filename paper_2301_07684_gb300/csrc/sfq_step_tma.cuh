@@ -45,16 +45,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
     }
     return false;
 }
-// Non-blocking test of the phase of parity `parity`.
-__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
@@ -131,8 +121,6 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
     constexpr int PPL = CFG::PPL;                          // particles per lane per tile
     constexpr int QS = CFG::QS;                            // one tile + a partial batch
     constexpr bool PAIRED = sizeof(T) == 4 && PPL == 2;     // adjacent-pair vector layout
-    // a warp's ring takes one tile's events on top of what it defers (at least a full batch)
-    static_assert(QS - PER_WARP >= 32, "event ring too small to defer a batch");
     extern __shared__ __align__(128) unsigned char smem[];
     QEntry<T> *wq = reinterpret_cast<QEntry<T> *>(smem + CFG::O_Q);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + CFG::O_BAR);
@@ -224,16 +212,7 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
         const int64_t tile = blockIdx.x + (int64_t)t * gridDim.x;
         if (tile >= ntiles) break;
         const int s = t % TMA_NSTAGE;
-        const uint32_t par = (t / TMA_NSTAGE) & 1;
-        // while the stage is still in flight, sample queued events: their latency then falls
-        // in the wait for the data instead of holding up the stages the other warps share
-        while (tail - head >= 32u && !__shfl_sync(0xFFFFFFFFu, (int)mbar_test(&full[s], par), 0)) {
-            const QEntry<T> e = q[(head + lane) & (QS - 1)];
-            __syncwarp();
-            head += 32;
-            process_events<T, TRUNC, false, SURR>(a, e.i, e.g, e.chi, (T)-1, e.px, e.py, e.pz, (uint8_t)e.fl, true, c);
-        }
-        if (!mbar_wait(&full[s], par)) {
+        if (!mbar_wait(&full[s], (t / TMA_NSTAGE) & 1)) {
             raise_timeout(a.counters);
             *(volatile int *)abort_flag = 1;
             break;
@@ -403,9 +382,7 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);        // this warp is done with the stage
-        // full batches wait for the next stage's wait, as long as the ring keeps room for
-        // the next tile's events (at most PER_WARP)
-        while (tail - head > (unsigned)(QS - PER_WARP)) {
+        while (tail - head >= 32u) {
             const QEntry<T> e = q[(head + lane) & (QS - 1)];
             __syncwarp();
             head += 32;
