@@ -409,7 +409,7 @@ sfq_status sfq_cascade_compact(sfq_ctx *ctx, const sfq_particles *src, const sfq
         return fail(ctx, SFQ_ERR_ARG, "compaction: scratch null, misaligned or too small");
     DeviceGuard g(ctx->device);
     const cudaError_t e = sfq::launch_compact(ctx->cfg.precision, *src, *fsrc, *dst, *fdst, scratch,
-                                              (cudaStream_t)stream);
+                                              (cudaStream_t)stream, ctx->num_sms);
     return e == cudaSuccess ? SFQ_OK : cuda_fail(ctx, e, "sfq_cascade_compact");
 }
 

@@ -8,8 +8,8 @@ namespace sfq {
 namespace {
 
 constexpr int CB = 256;              // threads per block of the compaction
-constexpr int CE = 4;                // chunks of CB consecutive particles per block
-constexpr int CPB = CB * CE;         // particles per block
+constexpr int CG_PER_SM = 8;         // compaction blocks per SM (the grid)
+constexpr int CG_MAX = 4096;         // largest compaction grid (bounds the scratch)
 constexpr int SCAN_BS = 1024;        // the single block of the scan
 
 // begin: clamp the live count to the capacity and start the append counter there; after a
@@ -29,18 +29,25 @@ __device__ __forceinline__ int64_t live_count(const unsigned long long *count, i
     return m < n ? m : n;
 }
 
-// Alive particles of each block's CPB-particle range.
+// The contiguous share [lo, hi) of the live range [0, m) that block b of g takes, in whole
+// chunks of CB particles, so that the blocks' shares keep the particles' order.
+__device__ __forceinline__ void block_share(int64_t m, int b, int g, int64_t &lo, int64_t &hi) {
+    const int64_t chunks = (m + CB - 1) / CB;
+    const int64_t per = (chunks + g - 1) / g;
+    lo = (int64_t)b * per * CB;
+    hi = lo + per * CB;
+    lo = lo < m ? lo : m;
+    hi = hi < m ? hi : m;
+}
+
+// Alive particles of each block's share of the live range.
 __global__ void __launch_bounds__(CB) compact_count_kernel(const uint8_t *flags, const unsigned long long *count,
                                                            int64_t n, uint32_t *block_alive) {
     __shared__ int ws[CB / 32];
-    const int64_t m = live_count(count, n);
-    const int64_t base = (int64_t)blockIdx.x * CPB;
+    int64_t lo, hi;
+    block_share(live_count(count, n), blockIdx.x, gridDim.x, lo, hi);
     int k = 0;
-#pragma unroll
-    for (int e = 0; e < CE; ++e) {
-        const int64_t i = base + e * CB + threadIdx.x;
-        k += (i < m && (flags[i] & SFQ_ALIVE)) ? 1 : 0;
-    }
+    for (int64_t i = lo + threadIdx.x; i < hi; i += CB) k += (flags[i] & SFQ_ALIVE) ? 1 : 0;
     k = __reduce_add_sync(0xFFFFFFFFu, k);
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = k;
     __syncthreads();
@@ -111,17 +118,17 @@ struct CompactArgs {
 };
 
 // Each alive particle goes to its block's offset plus the alive particles before it in the
-// block: chunk by chunk, warp ballots and the warps' counts in shared memory.
+// block's share: chunk by chunk, warp ballots and the warps' counts in shared memory.
 template <typename T>
 __global__ void __launch_bounds__(CB) compact_scatter_kernel(const CompactArgs<T> a) {
     __shared__ int ws[CB / 32];
-    const int64_t m = live_count(a.count, a.n);
-    const int64_t base = (int64_t)blockIdx.x * CPB;
+    int64_t lo, hi;
+    block_share(live_count(a.count, a.n), blockIdx.x, gridDim.x, lo, hi);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long off = a.block_off[blockIdx.x];
-    for (int e = 0; e < CE; ++e) {
-        const int64_t i = base + e * CB + threadIdx.x;
-        const bool alive = i < m && (a.flags[i] & SFQ_ALIVE);
+    for (int64_t c0 = lo; c0 < hi; c0 += CB) {                 // block-uniform trip count
+        const int64_t i = c0 + threadIdx.x;
+        const bool alive = i < hi && (a.flags[i] & SFQ_ALIVE);
         const unsigned bal = __ballot_sync(0xFFFFFFFFu, alive);
         if (lane == 0) ws[warp] = __popc(bal);
         __syncthreads();
@@ -150,12 +157,18 @@ __global__ void __launch_bounds__(CB) compact_scatter_kernel(const CompactArgs<T
     }
 }
 
-int64_t blocks_of(int64_t n) { return (n + CPB - 1) / CPB; }
+// Compaction grid: CG_PER_SM blocks per SM, no more blocks than chunks of the capacity.
+int64_t grid_of(int64_t capacity, int num_sms) {
+    const int64_t chunks = (capacity + CB - 1) / CB;
+    int64_t g = (int64_t)CG_PER_SM * (num_sms > 0 ? num_sms : 1);
+    g = g < CG_MAX ? g : CG_MAX;
+    return chunks < g ? chunks : g;
+}
 
 template <typename T>
 cudaError_t compact_t(const sfq_particles &src, const sfq_fields &fsrc, const sfq_particles &dst,
-                      const sfq_fields &fdst, void *scratch, cudaStream_t s) {
-    const int64_t nb = blocks_of(src.n);
+                      const sfq_fields &fdst, void *scratch, cudaStream_t s, int num_sms) {
+    const int64_t nb = grid_of(src.n, num_sms);
     if (nb == 0) {
         return cudaMemsetAsync(const_cast<unsigned long long *>(dst.n_dev), 0, sizeof(unsigned long long), s);
     }
@@ -201,14 +214,16 @@ cudaError_t launch_cascade_sync(unsigned long long *count, unsigned long long *n
 }
 
 size_t compact_scratch_bytes(int64_t capacity) {
-    const int64_t nb = blocks_of(capacity < 0 ? 0 : capacity);
+    // the largest grid any device gets (CG_MAX blocks), so the size needs no device
+    const int64_t chunks = ((capacity < 0 ? 0 : capacity) + CB - 1) / CB;
+    const int64_t nb = chunks < CG_MAX ? chunks : CG_MAX;
     return (size_t)(nb * (int64_t)(sizeof(unsigned long long) + sizeof(uint32_t)) + 16);
 }
 
 cudaError_t launch_compact(int precision, const sfq_particles &src, const sfq_fields &fsrc, const sfq_particles &dst,
-                           const sfq_fields &fdst, void *scratch, cudaStream_t s) {
-    return precision == SFQ_FP64 ? compact_t<double>(src, fsrc, dst, fdst, scratch, s)
-                                 : compact_t<float>(src, fsrc, dst, fdst, scratch, s);
+                           const sfq_fields &fdst, void *scratch, cudaStream_t s, int num_sms) {
+    return precision == SFQ_FP64 ? compact_t<double>(src, fsrc, dst, fdst, scratch, s, num_sms)
+                                 : compact_t<float>(src, fsrc, dst, fdst, scratch, s, num_sms);
 }
 
 }  // namespace sfq

@@ -115,7 +115,7 @@ cudaError_t launch_cascade_sync(unsigned long long *count, unsigned long long *n
                                 cudaStream_t s);
 size_t compact_scratch_bytes(int64_t capacity);
 cudaError_t launch_compact(int precision, const sfq_particles &src, const sfq_fields &fsrc, const sfq_particles &dst,
-                           const sfq_fields &fdst, void *scratch, cudaStream_t s);
+                           const sfq_fields &fdst, void *scratch, cudaStream_t s, int num_sms);
 // One CTA whose bounded mbarrier wait gives up after `polls` polls (sfq_check_bounded_wait).
 cudaError_t launch_wait_check(uint32_t polls, sfq_counters *c, cudaStream_t s);
 // Dynamic shared-memory attributes of every kernel shape (before graph capture).

@@ -697,11 +697,23 @@ __global__ void __launch_bounds__(IT, INFER_MINB) infer_tc_kernel(const InferArg
     const int64_t ntiles = (n_all + IT - 1) / IT;
     int pending = 0;                              // an MMA group issued and not yet waited for
 
+    // the inputs of the block's next tile are loaded a tile ahead, so that their latency falls
+    // in the current tile's work
+    float chi_n = 1.0f, r_n = 0.5f;
+    {
+        const int64_t i0 = (int64_t)blockIdx.x * IT + tid;
+        if (i0 < n_all) { chi_n = a.chi[i0]; r_n = a.r[i0]; }
+    }
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t i = tile * IT + tid;
         const bool valid = i < n_all;
-        const float chi = valid ? a.chi[i] : 1.0f;
-        const float r = valid ? a.r[i] : 0.5f;
+        const float chi = chi_n, r = r_n;
+        {
+            const int64_t inext = (tile + gridDim.x) * IT + tid;
+            chi_n = 1.0f;
+            r_n = 0.5f;
+            if (inext < n_all) { chi_n = a.chi[inext]; r_n = a.r[inext]; }
+        }
         const bool bad = !(chi >= 0.0f) || !(r > 0.0f) || !(r < 1.0f);
         const float rp = 2.0f * r - 1.0f;                 // pair creation: r' (exact for r in (0, 1))
         const float u = a.K.pair ? fabsf(rp) : r;

@@ -17,7 +17,7 @@
 namespace sfq {
 namespace {
 
-constexpr int SORT_TILE = 32 * 256;      // records per block (one warp, 256 rounds)
+constexpr int SORT_TILE = 32 * 64;       // records per block (one warp, 64 rounds)
 constexpr int RADIX = 256;
 
 __global__ void keys_kernel(int64_t n, const uint64_t *__restrict__ pid, const uint32_t *__restrict__ step,

@@ -252,13 +252,17 @@ __device__ __forceinline__ bool blcfa_phase_a(const StepArgs<T> &a, const T *s_n
         a.flags[i] = (uint8_t)(fl & ~SFQ_JUST_CREATED);
         return false;
     }
+    // the stored history first, all six loads together (the stores below could alias them)
+    T fpv[3], dfv[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { fpv[k] = a.fprev[k][i]; dfv[k] = a.dfprev[k][i]; }
+    const uint64_t id = a.id ? a.id[i] : a.id_base + (uint64_t)i;
     T d1[3], Fd2 = (T)0, FFdd = (T)0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const T fpv = a.fprev[k][i], dfv = a.dfprev[k][i];
-        d1[k] = F[k] - fpv;
+        d1[k] = F[k] - fpv[k];
         const T fd = d1[k] * a.inv_dt;
-        const T fdd = (d1[k] - dfv) * a.inv_dt2;
+        const T fdd = (d1[k] - dfv[k]) * a.inv_dt2;
         Fd2 = fma(fd, fd, Fd2);
         FFdd = fma(F[k], fdd, FFdd);
         a.fprev[k][i] = F[k];
@@ -269,7 +273,6 @@ __device__ __forceinline__ bool blcfa_phase_a(const StepArgs<T> &a, const T *s_n
     const T zeta = (T)2.220446049250313080847263336181640625e-16;
     const T zeta2 = (T)4.930380657631323783823303533017413935457540219431393779648e-32;
     const bool gate = (D > zeta2 * F2 * F2) && (chi > zeta);
-    const uint64_t id = a.id ? a.id[i] : a.id_base + (uint64_t)i;
     const u4 w = draws(a.seed, id, a.step, (fl >> SFQ_TAG_SHIFT) & 3u);
     const T r0 = uniform<T>(w.w[0]);
     // Acceptance-rejection of the local method (Sec. 2): W~_rad(chi) <= W~_rad(0) = 5 pi / 2,
