@@ -593,10 +593,12 @@ def run_ours(args):
         r.scratch = torch.empty(sfq.cascade_compact_scratch_bytes(r.A.cap), dtype=torch.uint8, device=device)
         torch.cuda.synchronize()
         e0.record()
-        n_after = r.compact()
+        ctx.cascade_compact(r.A.P, r.A.F, r.B.P, r.B.F, r.scratch)
         e1.record()
         torch.cuda.synchronize()
         ms_compact = e0.elapsed_time(e1)
+        r.A, r.B = r.B, r.A
+        n_after = r.count()
         # algorithmic bytes: the flags read by the count and the scatter passes (1 B each per
         # particle), and each alive particle's columns read and written (p 12, tau 8, id 8,
         # flags 1, phase index 4 = 33 B in binary32)

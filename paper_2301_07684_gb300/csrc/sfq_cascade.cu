@@ -128,7 +128,22 @@ __global__ void __launch_bounds__(CB) compact_scatter_kernel(const CompactArgs<T
     unsigned long long off = a.block_off[blockIdx.x];
     for (int64_t c0 = lo; c0 < hi; c0 += CB) {                 // block-uniform trip count
         const int64_t i = c0 + threadIdx.x;
-        const bool alive = i < hi && (a.flags[i] & SFQ_ALIVE);
+        const bool in = i < hi;
+        // the particle's columns are loaded before the ranking, so that their latency
+        // overlaps the ballot and the block's count exchange
+        const uint8_t fl = in ? a.flags[i] : (uint8_t)0;
+        T px = (T)0, py = (T)0, pz = (T)0, am = (T)0;
+        double ta = 0.0;
+        uint64_t idv = 0;
+        uint32_t kv = 0;
+        if (in) {
+            px = a.px[i]; py = a.py[i]; pz = a.pz[i];
+            ta = a.tau[i];
+            idv = a.id[i];
+            kv = a.k0[i];
+            if (a.amp) am = a.amp[i];
+        }
+        const bool alive = in && (fl & SFQ_ALIVE);
         const unsigned bal = __ballot_sync(0xFFFFFFFFu, alive);
         if (lane == 0) ws[warp] = __popc(bal);
         __syncthreads();
@@ -141,12 +156,12 @@ __global__ void __launch_bounds__(CB) compact_scatter_kernel(const CompactArgs<T
         }
         if (alive) {
             const unsigned long long j = off + (unsigned long long)(before + __popc(bal & ((1u << lane) - 1u)));
-            a.dpx[j] = a.px[i]; a.dpy[j] = a.py[i]; a.dpz[j] = a.pz[i];
-            a.dtau[j] = a.tau[i];
-            a.did[j] = a.id[i];
-            a.dflags[j] = a.flags[i];
-            a.dk0[j] = a.k0[i];
-            if (a.amp) a.damp[j] = a.amp[i];
+            a.dpx[j] = px; a.dpy[j] = py; a.dpz[j] = pz;
+            a.dtau[j] = ta;
+            a.did[j] = idv;
+            a.dflags[j] = fl;
+            a.dk0[j] = kv;
+            if (a.amp) a.damp[j] = am;
             if (a.fp[0]) {
 #pragma unroll
                 for (int d3 = 0; d3 < 3; ++d3) { a.dfp[d3][j] = a.fp[d3][i]; a.ddf[d3][j] = a.df[d3][i]; }
