@@ -762,7 +762,7 @@ def run_ours(args):
         table = torch.as_tensor(d["table"]).to(device=device, dtype=dtype)
         k0 = torch.as_tensor(d["k0"].view(np.int32)).to(device)
         F = sfq.FieldSource.plane_wave(k0, table, d["k_step"], amp0=d["amp0"])
-        steps, warm = args.steps, args.warmup
+        steps, warm = args.fused_steps, args.warmup
         out = sfq.ProductBuffers(int(0.09 * n * (steps + 1)) + 4096, dtype, device)
         cnt = sfq.counters_tensor(device)
         ctx.mc_run_fused(P, F, 0, warm, out, counters=cnt)            # warm-up steps
@@ -1090,6 +1090,8 @@ def main():
     ap.add_argument("--surrogate-steps", type=int, default=30000,
                     help="training steps of the surrogate leg (0 skips it)")
     ap.add_argument("--fused", type=int, default=1, help="time the fused multi-step plane-wave run (0: skip)")
+    ap.add_argument("--fused-steps", type=int, default=200,
+                    help="steps in the one timed launch of the fused run (the run it stands for is long)")
     ap.add_argument("--cascade-steps", type=int, default=100, help="steps of the full-cascade leg")
     ap.add_argument("--config3-steps", type=int, default=100, help="steps of the config-3 leg (0 skips it)")
     ap.add_argument("--config3-oracle-photons", type=int, default=32,
