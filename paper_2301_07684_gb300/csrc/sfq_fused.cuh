@@ -14,10 +14,8 @@
 // that ends in an event puts the slot on the warp's event queue and the slot waits; the
 // other slots keep stepping.  The queue is sampled 32 events at a time, the parents' new
 // states are handed back through shared memory and the waiting slots resume.  A partial
-// batch is sampled only when no slot of the warp can step.  A slot whose particle has
-// taken all its steps stores it and takes the next particle of the warp's share.  So the
-// sampler, whose cost is per batch, runs on full batches except at the end of the share,
-// and lanes idle only there.
+// batch is sampled only when no slot of the warp can step.  So the sampler, whose cost is
+// per batch, always runs on full batches except at the end of a chunk of particles.
 #pragma once
 #include "sfq_step.cuh"
 
@@ -70,131 +68,116 @@ __global__ void __launch_bounds__(FUSED_BS, 2) mc_fused_kernel(const StepArgs<T>
 
     Cnt c;
     c.zero();
+    constexpr int CH = 32 * PPL;
     const int64_t n_eff = effective_n(a);
-    // each warp steps a contiguous share of the particles; a slot whose particle has taken
-    // all its steps (or died) stores it and takes the share's next one, so that lanes do not
-    // idle at the end of every group of particles, only at the end of the share
+    const int64_t nchunks = (n_eff + CH - 1) / CH;
     const int64_t gw = (int64_t)blockIdx.x * CFG::WARPS + warp, nw = (int64_t)gridDim.x * CFG::WARPS;
-    const int64_t per = (((n_eff + nw - 1) / nw) + 31) / 32 * 32;
-    const int64_t w0 = gw * per < n_eff ? gw * per : n_eff;
-    const int64_t w1 = w0 + per < n_eff ? w0 + per : n_eff;
-    const unsigned lt = (1u << lane) - 1u;
-    T px[PPL], py[PPL], pz[PPL], amp[PPL];
-    double tau[PPL];
-    uint32_t rel[PPL];                          // the slot's particle: w0 + rel
-    uint32_t fl[PPL], st[PPL], off[PPL], k0[PPL], pos[PPL];
-    bool pend[PPL], in[PPL];
-    int64_t next = w0;                          // warp-uniform: the share's next particle
-    const auto take = [&](int k, int64_t i) {
-        rel[k] = (uint32_t)(i - w0);
-        in[k] = i < w1;
-        px[k] = py[k] = pz[k] = amp[k] = (T)0;
-        tau[k] = 0.0;
-        fl[k] = 0u;
-        k0[k] = 0u;
-        if (in[k]) {
-            px[k] = a.px[i]; py[k] = a.py[i]; pz[k] = a.pz[i];
-            tau[k] = a.tau[i];
-            fl[k] = a.flags[i];
-            k0[k] = a.k0[i];
-            amp[k] = a.amp ? a.amp[i] : a.amp0;
-        }
-        st[k] = 0u;
-        off[k] = off0;
-        pend[k] = false;
-        pos[k] = 0u;
-    };
-#pragma unroll
-    for (int k = 0; k < PPL; ++k) take(k, next + k * 32 + lane);
-    next += 32 * PPL;
-    unsigned qt = 0, qh = 0;                    // warp-uniform queue tail and head
-    for (;;) {
-        bool ran = false;
+    for (int64_t ch = gw; ch < nchunks; ch += nw) {
+        const int64_t base = ch * CH;
+        T px[PPL], py[PPL], pz[PPL], amp[PPL];
+        double tau[PPL];
+        uint32_t fl[PPL], st[PPL], off[PPL], k0[PPL], pos[PPL];
+        bool pend[PPL], in[PPL];
 #pragma unroll
         for (int k = 0; k < PPL; ++k) {
-            const int64_t i = w0 + rel[k];
-            const bool run = in[k] && (fl[k] & SFQ_ALIVE) && !pend[k] && st[k] < nsteps;
-            bool ev = false;
-            T g = (T)0, chi = (T)0;
-            if (run) {
-                ran = true;
-                uint32_t kk = k0[k] + off[k];               // as the per-step field source
-                kk -= (kk >= K) ? K : 0u;
-                kk = kk < K ? kk : K - 1u;
-                const T f = amp[k] * s_tab[kk];
-                const T E[3] = {(T)0, f, (T)0}, B[3] = {(T)0, (T)0, f};
-                ev = step_particle_v<T, true>(a, s_nlc, s_nbw, i, (uint8_t)fl[k], px[k], py[k], pz[k], E, B,
-                                              tau[k], g, chi, c, step0 + st[k]);
-                if (!ev) {
-                    ++st[k];
-                    off[k] += kstep;
-                    off[k] -= (off[k] >= K) ? K : 0u;
-                }
+            const int64_t i = base + k * 32 + lane;
+            in[k] = i < n_eff;
+            px[k] = py[k] = pz[k] = amp[k] = (T)0;
+            tau[k] = 0.0;
+            fl[k] = 0u;
+            k0[k] = 0u;
+            if (in[k]) {
+                px[k] = a.px[i]; py[k] = a.py[i]; pz[k] = a.pz[i];
+                tau[k] = a.tau[i];
+                fl[k] = a.flags[i];
+                k0[k] = a.k0[i];
+                amp[k] = a.amp ? a.amp[i] : a.amp0;
             }
-            const unsigned m = __ballot_sync(0xFFFFFFFFu, ev);
-            if (ev) {
-                const unsigned r = qt + __popc(m & lt);
-                FEntry<T> e;
-                e.i = i;
-                e.g = g;
-                e.chi = chi;
-                e.px = px[k]; e.py = py[k]; e.pz = pz[k];
-                e.step = step0 + st[k];
-                e.fl = fl[k];
-                q[r & (QS - 1)] = e;
-                pend[k] = true;
-                pos[k] = r;
-            }
-            qt += __popc(m);
+            st[k] = 0u;
+            off[k] = off0;
+            pend[k] = false;
+            pos[k] = 0u;
         }
-        const bool any_ran = __any_sync(0xFFFFFFFFu, ran);
-        bool any_in = false;
-#pragma unroll
-        for (int k = 0; k < PPL; ++k) any_in |= in[k];
-        if (!__any_sync(0xFFFFFFFFu, any_in) && qt == qh) break;     // the share is done
-        // sample full batches; a partial one only when no slot could step
-        while (qt - qh >= 32u || (!any_ran && qt != qh)) {
-            __syncwarp();
-            const unsigned nb = qt - qh < 32u ? qt - qh : 32u;
-            const bool v = (unsigned)lane < nb;
-            FEntry<T> e{};
-            if (v) e = q[(qh + lane) & (QS - 1)];
-            EvOut<T> o;
-            process_events_core<T, TRUNC>(a, e.step, e.i, e.g, e.chi, (T)-1, e.px, e.py, e.pz, (uint8_t)e.fl, v,
-                                          c, o);
-            if (v) res[(qh + lane) & (QS - 1)] = o;
-            __syncwarp();
-            // the waiting slots take their new state and finish their step
+        unsigned qt = 0, qh = 0;               // warp-uniform queue tail and head
+        for (;;) {
+            bool ran = false;
 #pragma unroll
             for (int k = 0; k < PPL; ++k) {
-                if (pend[k] && pos[k] - qh < nb) {
-                    const EvOut<T> r = res[pos[k] & (QS - 1)];
-                    if (r.what & 1) { px[k] = r.px; py[k] = r.py; pz[k] = r.pz; }
-                    if (r.what & 2) tau[k] = r.tau;
-                    if (r.what & 4) fl[k] = r.fl;
-                    pend[k] = false;
-                    ++st[k];
-                    off[k] += kstep;
-                    off[k] -= (off[k] >= K) ? K : 0u;
+                const int64_t i = base + k * 32 + lane;
+                const bool run = in[k] && (fl[k] & SFQ_ALIVE) && !pend[k] && st[k] < nsteps;
+                bool ev = false;
+                T g = (T)0, chi = (T)0;
+                if (run) {
+                    ran = true;
+                    uint32_t kk = k0[k] + off[k];               // as the per-step field source
+                    kk -= (kk >= K) ? K : 0u;
+                    kk = kk < K ? kk : K - 1u;
+                    const T f = amp[k] * s_tab[kk];
+                    const T E[3] = {(T)0, f, (T)0}, B[3] = {(T)0, (T)0, f};
+                    ev = step_particle_v<T, true>(a, s_nlc, s_nbw, i, (uint8_t)fl[k], px[k], py[k], pz[k], E, B,
+                                                  tau[k], g, chi, c, step0 + st[k]);
+                    if (!ev) {
+                        ++st[k];
+                        off[k] += kstep;
+                        off[k] -= (off[k] >= K) ? K : 0u;
+                    }
                 }
+                const unsigned m = __ballot_sync(0xFFFFFFFFu, ev);
+                if (ev) {
+                    const unsigned r = qt + __popc(m & ((1u << lane) - 1u));
+                    FEntry<T> e;
+                    e.i = i;
+                    e.g = g;
+                    e.chi = chi;
+                    e.px = px[k]; e.py = py[k]; e.pz = pz[k];
+                    e.step = step0 + st[k];
+                    e.fl = fl[k];
+                    q[r & (QS - 1)] = e;
+                    pend[k] = true;
+                    pos[k] = r;
+                }
+                qt += __popc(m);
             }
-            qh += nb;
-            if (!any_ran) break;                      // re-check which slots can step
+            const bool any_ran = __any_sync(0xFFFFFFFFu, ran);
+            if (!any_ran && qt == qh) break;              // every slot finished
+            // sample full batches; a partial one only when no slot could step
+            while (qt - qh >= 32u || (!any_ran && qt != qh)) {
+                __syncwarp();
+                const unsigned nb = qt - qh < 32u ? qt - qh : 32u;
+                const bool v = (unsigned)lane < nb;
+                FEntry<T> e{};
+                if (v) e = q[(qh + lane) & (QS - 1)];
+                EvOut<T> o;
+                process_events_core<T, TRUNC>(a, e.step, e.i, e.g, e.chi, (T)-1, e.px, e.py, e.pz, (uint8_t)e.fl, v,
+                                              c, o);
+                if (v) res[(qh + lane) & (QS - 1)] = o;
+                __syncwarp();
+                // the waiting slots take their new state and finish their step
+#pragma unroll
+                for (int k = 0; k < PPL; ++k) {
+                    if (pend[k] && pos[k] - qh < nb) {
+                        const EvOut<T> r = res[pos[k] & (QS - 1)];
+                        if (r.what & 1) { px[k] = r.px; py[k] = r.py; pz[k] = r.pz; }
+                        if (r.what & 2) tau[k] = r.tau;
+                        if (r.what & 4) fl[k] = r.fl;
+                        pend[k] = false;
+                        ++st[k];
+                        off[k] += kstep;
+                        off[k] -= (off[k] >= K) ? K : 0u;
+                    }
+                }
+                qh += nb;
+                if (!any_ran) break;                      // re-check which slots can step
+            }
         }
-        // finished slots store their particle and take the next ones of the share
 #pragma unroll
         for (int k = 0; k < PPL; ++k) {
-            const bool fin = in[k] && !pend[k] && (st[k] >= nsteps || !(fl[k] & SFQ_ALIVE));
-            const unsigned m = __ballot_sync(0xFFFFFFFFu, fin);
-            if (m == 0u) continue;
-            if (fin) {
-                const int64_t i = w0 + rel[k];
+            const int64_t i = base + k * 32 + lane;
+            if (in[k]) {
                 a.px[i] = px[k]; a.py[i] = py[k]; a.pz[i] = pz[k];
                 a.tau[i] = tau[k];
                 a.flags[i] = (uint8_t)fl[k];
-                take(k, next + __popc(m & lt));
             }
-            next += __popc(m);
         }
     }
     flush_counters(c, a.counters);
