@@ -236,8 +236,8 @@ def run_ours(args):
             fs = lambda s: F
         # launch shape from the autotuner (timed on a copy of the population)
         if args.shape:
-            v, sh = (int(x) for x in args.shape.split(":"))
-            ctx.set_step_shape(v, sh, 0)
+            v, sh, *g = (int(x) for x in args.shape.split(":"))
+            ctx.set_step_shape(v, sh, g[0] if g else 0)
             tuned = (v, sh, None)
         else:
             tuned = ctx.autotune_step(P, fs(0), 0)
@@ -1100,7 +1100,7 @@ def main():
     ap.add_argument("--legs", default="config1,pw,fp64,trunc,fused,fused64,batched,cascade,config3,evaluators,surrogate",
                     help="legs timed beside the headline step (comma list; the headline always runs)")
     ap.add_argument("--shape", default="",
-                    help="fixed launch shape 'variant:shape' of the per-step legs (e.g. 2:16) instead of the autotuner")
+                    help="fixed launch shape 'variant:shape[:grid]' of the per-step legs (e.g. 2:16) instead of the autotuner")
     ap.add_argument("--oracle-config1", type=int, default=1, help="also time the oracle on config 1 (0: skip)")
     ap.add_argument("--oracle-particles", type=int, default=512,
                     help="sampled particles of the timed run the oracle replays (CPU baseline and parity sample)")

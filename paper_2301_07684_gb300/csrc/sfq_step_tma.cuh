@@ -4,8 +4,10 @@
 // slices (momenta, optical depth, flags, fields or phase index) from global to
 // shared memory with 1D bulk copies (cp.async.bulk), NSTAGE tiles ahead, and 16
 // consumer warps compute the step (Sec. 2 and 4 of Montefiori & Tamburini,
-// arXiv:2301.07684) from shared memory.  Each consumer warp queues its event particles,
-// with the state it read, in a ring of its own and samples them 32 at a time.  Stages are handed over with mbarriers
+// arXiv:2301.07684) from shared memory.  A tile is cut into one slice per consumer warp;
+// with fields in memory the warps claim the slices in order from a shared counter, so a
+// warp busy with its events delays no stage's release.  Each consumer warp queues its event particles, with the
+// state it read, in a ring of its own and samples them 32 at a time.  Stages are handed over with mbarriers
 // (full: producer -> consumers, completed by the copies' transaction bytes;
 // empty: consumers -> producer).  Every wait is bounded: on a timeout the kernel
 // raises the timeout word of the counters and leaves its loops after its copies
@@ -126,6 +128,7 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + CFG::O_BAR);
     uint64_t *empty = full + TMA_NSTAGE;
     int *abort_flag = reinterpret_cast<int *>(empty + TMA_NSTAGE);
+    unsigned *slice_ctr = reinterpret_cast<unsigned *>(empty + TMA_NSTAGE + 1);
     using RS = RateSmem<T>;
     __shared__ __align__(16) T s_nlc[RS::NLC_N];
     __shared__ __align__(16) T s_nbw[RS::NBW_N];
@@ -141,6 +144,7 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
             mbar_init(&empty[s], TMA_CONSUMER_WARPS);
         }
         *abort_flag = 0;
+        *slice_ctr = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -208,11 +212,25 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
     unsigned head = 0, tail = 0;
     Cnt c;
     c.zero();
-    for (int t = 0;; ++t) {
+    // With fields in memory (SoA) the step waits on HBM and on its events: a warp takes the
+    // block's next slice (one warp's share, PER_WARP particles, of tile t) from a shared
+    // counter, so a warp that is sampling its events leaves the next slices to the others
+    // instead of holding up the release of their stage.  Slices are claimed in order and each
+    // warp holds one claim, so no warp can wait on a stage two phases ahead.  With the plane
+    // wave the step is bound by issue, and warp w keeps slice w of every tile (no claim).
+    constexpr bool CLAIM = FK == FK_SOA;
+    for (unsigned it = 0;; ++it) {
+        unsigned g = it * TMA_CONSUMER_WARPS + (unsigned)warp;
+        if constexpr (CLAIM) {
+            if (lane == 0) g = atomicAdd(slice_ctr, 1u);
+            g = __shfl_sync(0xFFFFFFFFu, g, 0);
+        }
+        const unsigned t = g / TMA_CONSUMER_WARPS;
+        const int sl = (int)(g % TMA_CONSUMER_WARPS);
         const int64_t tile = blockIdx.x + (int64_t)t * gridDim.x;
         if (tile >= ntiles) break;
-        const int s = t % TMA_NSTAGE;
-        if (!mbar_wait(&full[s], (t / TMA_NSTAGE) & 1)) {
+        const int s = (int)(t % TMA_NSTAGE);
+        if (!mbar_wait(&full[s], (t / TMA_NSTAGE) & 1u)) {
             raise_timeout(a.counters);
             *(volatile int *)abort_flag = 1;
             break;
@@ -230,7 +248,7 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
         uint8_t fk[PPL];
         if (staged && PAIRED) {
             // full tile, binary32: lane takes the adjacent particles li0, li0 + 1 (vector loads)
-            const int li0 = warp * PER_WARP + 2 * lane;
+            const int li0 = sl * PER_WARP + 2 * lane;
             const float2 vx = *reinterpret_cast<const float2 *>(spx + li0);
             const float2 vy = *reinterpret_cast<const float2 *>(spy + li0);
             const float2 vz = *reinterpret_cast<const float2 *>(spz + li0);
@@ -310,7 +328,7 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
             // full tile: everything from shared memory, no bounds checks
 #pragma unroll
             for (int k = 0; k < PPL; ++k) {
-                const int li = warp * PER_WARP + k * 32 + lane;
+                const int li = sl * PER_WARP + k * 32 + lane;
                 const uint8_t fl = sfl[li];
                 ev[k] = false;
                 gk[k] = (T)0;
@@ -342,7 +360,7 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
             // last, partial tile: global memory with bounds checks
 #pragma unroll
             for (int k = 0; k < PPL; ++k) {
-                const int li = warp * PER_WARP + k * 32 + lane;
+                const int li = sl * PER_WARP + k * 32 + lane;
                 const int64_t i = start + li;
                 ev[k] = false;
                 gk[k] = (T)0;
@@ -368,8 +386,8 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
             if (ev[k]) {
                 const unsigned r = __popc(m & ((1u << lane) - 1u));
                 QEntry<T> e;
-                e.i = (staged && PAIRED) ? start + warp * PER_WARP + 2 * lane + k
-                                         : start + warp * PER_WARP + k * 32 + lane;
+                e.i = (staged && PAIRED) ? start + sl * PER_WARP + 2 * lane + k
+                                         : start + sl * PER_WARP + k * 32 + lane;
                 e.g = gk[k];
                 e.chi = ck[k];
                 e.px = pk[k][0];
@@ -381,7 +399,7 @@ __global__ void __launch_bounds__(32 * (CW + 1), 1) mc_step_tma_kernel(const Ste
             tail += __popc(m);
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);        // this warp is done with the stage
+        if (lane == 0) mbar_arrive(&empty[s]);        // this slice of the stage is done
         while (tail - head >= 32u) {
             const QEntry<T> e = q[(head + lane) & (QS - 1)];
             __syncwarp();
