@@ -9,9 +9,9 @@
 // per-block gradient partials reduced in a fixed order, Adam).  With `quantize`, the
 // forward pass rounds the weights and the inputs of layers 2-4 to bfloat16 exactly as the
 // inference kernel does (the rounding is passed straight through in the backward pass).
-// Inference runs the two 64 x 64 layers on the tensor cores (tcgen05.mma, bfloat16
-// operands staged in shared memory, binary32 accumulators in tensor memory, read back
-// with tcgen05.ld); layers 1 and 4 and the SiLU epilogues run on the CUDA cores.  Cells
+// Inference runs layers 2-4 on the tensor cores (tcgen05.mma, bfloat16 operands staged in
+// shared memory, binary32 accumulators in tensor memory, read back with tcgen05.ld); layer
+// 1 and the SiLU epilogues run on the CUDA cores.  Cells
 // of (ln chi, u) where the network disagrees with the plain fitted sampler by more than a
 // tolerance in u (a bound on its contribution to the KS distance of the sampled energies)
 // are flagged by sfq_mlp_calibrate; draws in flagged cells, and chi outside the training
@@ -469,7 +469,8 @@ __global__ void plain_targets_kernel(const float *__restrict__ inv, const Kind K
 // Tensor-core inference.  One block of 128 threads handles tiles of 128 samples (one
 // sample per thread, one row of the 128 x 64 activation tile).  Layers 2 and 3 are
 //   D[128 x 64] (fp32, tensor memory) = A[128 x 64] (bf16, smem) * W^T (W: 64 x 64 bf16, smem)
-// issued as four K = 16 steps of tcgen05.mma.kind::f16 by one thread.  Operands use the
+// issued as four K = 16 steps of tcgen05.mma.kind::f16 by one thread; the output layer is
+// the same with a 16 x 64 W whose row 0 is w4 (column 0 of D is the output).  Operands use the
 // no-swizzle K-major layout: 8-row x 16-byte core matrices, core matrix (row group g, K
 // chunk j) at ((g * 8) + j) * 128 bytes, i.e. K-adjacent core matrices 128 bytes apart
 // (leading byte offset) and row groups 1024 bytes apart (stride byte offset).
@@ -479,6 +480,8 @@ constexpr uint32_t TMEM_COLS = 64;
 // kind::f16 instruction descriptor: D f32 (bit 4), A bf16 (bits 7-9 = 1), B bf16 (bits
 // 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+// the output layer: N = 16 (row 0 of its B operand holds w4, rows 1-15 are zero)
+constexpr uint32_t IDESC4 = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ uint32_t s_u32(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
@@ -505,11 +508,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void mma_k16(uint32_t d_tmem, uint64_t ad, uint64_t bd, uint32_t accumulate) {
+__device__ __forceinline__ void mma_k16(uint32_t d_tmem, uint64_t ad, uint64_t bd, uint32_t accumulate,
+                                        uint32_t idesc = IDESC) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-        "l"(ad), "l"(bd), "r"(IDESC), "r"(accumulate)
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
@@ -531,6 +535,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+}
+// Column 0 of this thread's lane.
+__device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr) : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    return __uint_as_float(r);
 }
 // Row m of a 128 x 64 (or 64 x 64) K-major operand: 8 chunks of 8 bf16 (16 bytes).
 __device__ __forceinline__ uint32_t row_chunk_offset(int m, int j) { return (uint32_t)((((m >> 3) * 8) + j) * 128 + (m & 7) * 16); }
@@ -577,10 +588,12 @@ __device__ __forceinline__ unsigned long long warp_reserve(unsigned long long *c
     return base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
 }
 
-constexpr uint32_t SM_A = 0, SM_B2 = 16384, SM_B3 = 24576, SM_SMALL = 32768;
-constexpr uint32_t SM_FLAGS = SM_SMALL + (H * 2 + 4 * H + 4) * 4;
+// Operands (no-swizzle K-major, 16-byte aligned): A 128 x 64, W2 and W3 64 x 64, W4 16 x 64;
+// then layer 1's weights, the halved biases of layers 2 and 3, b4 and the fallback flags.
+constexpr uint32_t SM_A = 0, SM_B2 = 16384, SM_B3 = 24576, SM_B4 = 32768, SM_SMALL = 34816;
+constexpr uint32_t SM_FLAGS = SM_SMALL + ((H * 2 + 3 * H + 1) * 4 + 15) / 16 * 16;
 constexpr uint32_t SM_BYTES = SM_FLAGS + NCELL / 8;    // the fallback flags as one bit per cell
-constexpr uint32_t INFER_SMEM = SM_BYTES + 1024;     // + alignment slack
+constexpr uint32_t INFER_SMEM = SM_BYTES + 128;      // + alignment slack
 #ifndef SFQ_INFER_MINB
 #define SFQ_INFER_MINB 6
 #endif
@@ -600,26 +613,19 @@ __device__ __forceinline__ uint4 pack8_bf16(const float *a) {
     return v;
 }
 
-// The epilogue of a tensor-core layer for this thread's row, 32 accumulator columns at a
-// time (so that no more than 32 accumulators are live): h = (d + b) / 2 from the halved
-// biases hb, SiLU, and either the bfloat16 row of the next layer's operand A (to_a) or the
-// output layer's dot product with w4 (acc).
-__device__ __forceinline__ void epilogue(uint32_t t_row, const float *hb, unsigned char *a_base, int row, bool to_a,
-                                         const float *w4, float &acc) {
+// The epilogue of a hidden tensor-core layer for this thread's row, 32 accumulator columns
+// at a time (so that no more than 32 accumulators are live): h = (d + b) / 2 from the
+// halved biases hb, SiLU, and the bfloat16 row of the next layer's operand A.
+__device__ __forceinline__ void epilogue(uint32_t t_row, const float *hb, unsigned char *a_base, int row) {
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
         float d[32];
         tmem_ld32(t_row + 32 * half, d);
 #pragma unroll
         for (int j = 0; j < 32; ++j) d[j] = silu_h(fmaf(0.5f, d[j], hb[32 * half + j]));
-        if (to_a) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-                *reinterpret_cast<uint4 *>(a_base + row_chunk_offset(row, 4 * half + c)) = pack8_bf16(d + 8 * c);
-        } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) acc = fmaf(bf16r(d[j]), w4[32 * half + j], acc);
-        }
+        for (int c = 0; c < 4; ++c)
+            *reinterpret_cast<uint4 *>(a_base + row_chunk_offset(row, 4 * half + c)) = pack8_bf16(d + 8 * c);
     }
 }
 
@@ -636,23 +642,29 @@ __global__ void __launch_bounds__(IT, INFER_MINB) infer_tc_kernel(const InferArg
     __shared__ uint32_t tmem_base;
     __shared__ int s_err;
     __shared__ unsigned long long s_cnt[6];
-    // 1024-byte aligned operand area
+    // 128-byte aligned operand area (the no-swizzle layout needs 16-byte alignment)
     const uint32_t raw = s_u32(sraw);
-    unsigned char *sm = sraw + ((1024u - (raw & 1023u)) & 1023u);
+    unsigned char *sm = sraw + ((128u - (raw & 127u)) & 127u);
     const uint32_t sbase = s_u32(sm);
     float *w1 = reinterpret_cast<float *>(sm + SM_SMALL);
-    float *b1 = w1 + 2 * H, *hb2 = b1 + H, *hb3 = hb2 + H, *w4 = hb3 + H, *b4 = w4 + H;
+    float *b1 = w1 + 2 * H, *hb2 = b1 + H, *hb3 = hb2 + H, *b4 = hb3 + H;
     uint32_t *fl = reinterpret_cast<uint32_t *>(sm + SM_FLAGS);
     const int tid = threadIdx.x, warp = tid >> 5;
     const float *P = a.params;
 
-    // weights: W2, W3 as bf16 in the K-major core-matrix layout; layer 1 and 4 binary32
-    // (bf16-rounded weights); the biases of layers 2 and 3 halved for the SiLU form
+    // weights: W2, W3 and W4 (row 0 of a 16-row operand, the other rows zero) as bf16 in the
+    // K-major core-matrix layout; layer 1 binary32 (bf16-rounded weights); the biases of
+    // layers 2 and 3 halved for the SiLU form
     for (int e = tid; e < H * H; e += IT) {
         const int n_ = e >> 6, k = e & 63;
         const uint32_t off = row_chunk_offset(n_, k >> 3) + (k & 7) * 2;
         *reinterpret_cast<__nv_bfloat16 *>(sm + SM_B2 + off) = __float2bfloat16_rn(P[O_W2 + e]);
         *reinterpret_cast<__nv_bfloat16 *>(sm + SM_B3 + off) = __float2bfloat16_rn(P[O_W3 + e]);
+    }
+    for (int e = tid; e < 16 * H; e += IT) {
+        const int n_ = e >> 6, k = e & 63;
+        const uint32_t off = row_chunk_offset(n_, k >> 3) + (k & 7) * 2;
+        *reinterpret_cast<__nv_bfloat16 *>(sm + SM_B4 + off) = __float2bfloat16_rn(n_ == 0 ? P[O_W4 + k] : 0.0f);
     }
     for (int e = tid; e < H; e += IT) {
         // layer 1 halved as well (exact: a power of two), so that h = z / 2 comes out of its fmas
@@ -661,7 +673,6 @@ __global__ void __launch_bounds__(IT, INFER_MINB) infer_tc_kernel(const InferArg
         b1[e] = 0.5f * P[O_B1 + e];
         hb2[e] = 0.5f * P[O_B2 + e];
         hb3[e] = 0.5f * P[O_B3 + e];
-        w4[e] = bf16r(P[O_W4 + e]);
     }
     if (tid == 0) *b4 = P[O_B4];
     for (int e = tid; e < NCELL / 32; e += IT) {
@@ -733,18 +744,20 @@ __global__ void __launch_bounds__(IT, INFER_MINB) infer_tc_kernel(const InferArg
             }
             *reinterpret_cast<uint4 *>(sm + SM_A + row_chunk_offset(tid, c)) = pack8_bf16(v);
         }
-        float y = *b4;
+        float y = 0.0f;
 #pragma unroll 1
-        for (int layer = 0; layer < 2; ++layer) {
+        for (int layer = 0; layer < 3; ++layer) {
             fence_async_smem();
             tc_fence_before();
             __syncthreads();
             if (tid == 0) {
                 tc_fence_after();
-                const uint32_t bw = layer == 0 ? SM_B2 : SM_B3;
+                const uint32_t bw = layer == 0 ? SM_B2 : (layer == 1 ? SM_B3 : SM_B4);
+                const uint32_t idesc = layer == 2 ? IDESC4 : IDESC;
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk)
-                    mma_k16(taddr, smem_desc(sbase + SM_A + 256 * kk), smem_desc(sbase + bw + 256 * kk), kk > 0);
+                    mma_k16(taddr, smem_desc(sbase + SM_A + 256 * kk), smem_desc(sbase + bw + 256 * kk), kk > 0,
+                            idesc);
                 mma_commit(&mbar);
             }
             pending = 1;
@@ -754,9 +767,10 @@ __global__ void __launch_bounds__(IT, INFER_MINB) infer_tc_kernel(const InferArg
             pending = 0;
             phase ^= 1;
             tc_fence_after();
-            // layer 2: the SiLU row goes to A (the MMA that read A has completed); layer 3:
-            // the output layer's dot product
-            epilogue(t_row, layer == 0 ? hb2 : hb3, sm + SM_A, tid, layer == 0, w4, y);
+            // layers 2 and 3: the SiLU row goes to A (the MMA that read A has completed); the
+            // output layer: column 0 plus b4
+            if (layer < 2) epilogue(t_row, layer == 0 ? hb2 : hb3, sm + SM_A, tid);
+            else y = tmem_ld1(t_row) + *b4;
             tc_fence_before();
         }
         if (s_err) break;
