@@ -1122,7 +1122,7 @@ def main():
                     help="FP64-pipe instructions per update of the binary64 step kernel (ncu capture)")
     ap.add_argument("--fp64-pipe-busy", type=float, default=0.874,
                     help="sm__pipe_fp64_cycles_active of the binary64 step kernel (ncu capture)")
-    ap.add_argument("--traffic-per-update", type=float, default=51.87,
+    ap.add_argument("--traffic-per-update", type=float, default=51.46,
                     help="DRAM bytes per update of the step kernel from an ncu capture (for roofline.traffic)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
