@@ -226,6 +226,14 @@ sfq_status sfq_counters_check(const sfq_counters *host_counters);
  * Asynchronous on `stream`. */
 sfq_status sfq_check_bounded_wait(sfq_ctx *ctx, uint32_t polls, sfq_counters *counters, void *stream);
 
+/* Check of the binary32 square roots every kernel uses for gamma = sqrt(1 + p^2), |p| and
+ * 1/gamma: the hardware reciprocal-square-root estimate refined by one Newton step (about
+ * 1 ulp).  For each of the n device values x[i] writes sqrt_out[i] (0 for x <= 0 or NaN)
+ * and rsqrt_out[i] (defined for finite x > 0), so that a test can compare them with
+ * correctly rounded results.  All pointers are device pointers of n floats (n >= 0; NULL only when
+ * n == 0).  Asynchronous on `stream`. */
+sfq_status sfq_check_sqrt(sfq_ctx *ctx, int64_t n, const float *x, float *sqrt_out, float *rsqrt_out, void *stream);
+
 /* One Monte Carlo step for every alive particle of `p` (Sec. 2 and 4; Sec. 5 for
  * BLCFA leptons):
  *   chi (Eq. chi_exact) -> rate (Eq. pe_rate_3 / Eq. pp_tot_real) -> leptons with

@@ -563,4 +563,13 @@ sfq_status sfq_check_bounded_wait(sfq_ctx *ctx, uint32_t polls, sfq_counters *co
     return e == cudaSuccess ? SFQ_OK : cuda_fail(ctx, e, "bounded-wait check");
 }
 
+sfq_status sfq_check_sqrt(sfq_ctx *ctx, int64_t n, const float *x, float *sqrt_out, float *rsqrt_out, void *stream) {
+    if (!ctx) return SFQ_ERR_ARG;
+    if (n < 0) return fail(ctx, SFQ_ERR_ARG, "n < 0");
+    if (n > 0 && (!x || !sqrt_out || !rsqrt_out)) return fail(ctx, SFQ_ERR_ARG, "null buffer");
+    DeviceGuard g(ctx->device);
+    const cudaError_t e = sfq::launch_sqrt_check(n, x, sqrt_out, rsqrt_out, ctx->num_sms, (cudaStream_t)stream);
+    return e == cudaSuccess ? SFQ_OK : cuda_fail(ctx, e, "square-root check");
+}
+
 }  // extern "C"

@@ -118,6 +118,7 @@ cudaError_t launch_compact(int precision, const sfq_particles &src, const sfq_fi
                            const sfq_fields &fdst, void *scratch, cudaStream_t s, int num_sms);
 // One CTA whose bounded mbarrier wait gives up after `polls` polls (sfq_check_bounded_wait).
 cudaError_t launch_wait_check(uint32_t polls, sfq_counters *c, cudaStream_t s);
+cudaError_t launch_sqrt_check(int64_t n, const float *x, float *so, float *ro, int num_sms, cudaStream_t s);
 // Dynamic shared-memory attributes of every kernel shape (before graph capture).
 cudaError_t prepare_step_f32();
 cudaError_t prepare_step_f64();

@@ -23,4 +23,21 @@ cudaError_t launch_wait_check(uint32_t polls, sfq_counters *c, cudaStream_t s) {
     wait_check_kernel<0><<<1, 32, 0, s>>>(polls, c);
     return cudaGetLastError();
 }
+
+// The kernels' binary32 square roots on n values (sfq_check_sqrt).
+__global__ void sqrt_check_kernel(int64_t n, const float *__restrict__ x, float *__restrict__ so,
+                                  float *__restrict__ ro) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = x[i];
+        so[i] = sqrt_nr(v);
+        ro[i] = rsqrt_nr(v);
+    }
+}
+cudaError_t launch_sqrt_check(int64_t n, const float *x, float *so, float *ro, int num_sms, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = (n + 255) / 256;
+    const int grid = (int)(blocks < (int64_t)num_sms * 8 ? blocks : (int64_t)num_sms * 8);
+    sqrt_check_kernel<<<grid, 256, 0, s>>>(n, x, so, ro);
+    return cudaGetLastError();
+}
 }  // namespace sfq

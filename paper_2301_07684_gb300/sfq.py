@@ -163,6 +163,8 @@ def lib():
         L.sfq_counters_check.restype = st
         L.sfq_check_bounded_wait.argtypes = [vp, u32, vp, vp]
         L.sfq_check_bounded_wait.restype = st
+        L.sfq_check_sqrt.argtypes = [vp, i64, vp, vp, vp, vp]
+        L.sfq_check_sqrt.restype = st
         L.sfq_version.restype = C.c_char_p
         _lib = L
     return _lib
@@ -176,7 +178,7 @@ EXPORTED = ["sfq_init", "sfq_finalize", "sfq_last_error", "sfq_constants", "sfq_
             "sfq_mlp_loss_grad", "sfq_mlp_train", "sfq_mlp_predict_lnw", "sfq_mlp_plain_targets", "sfq_mlp_calibrate",
             "sfq_mlp_sample_photon_xi", "sfq_mlp_create_pair", "sfq_mlp_sample_pair_xi",
             "sfq_cascade_run", "sfq_cascade_compact_scratch_bytes", "sfq_cascade_compact", "sfq_set_evaluator",
-            "sfq_table_pieces", "sfq_counters_check", "sfq_check_bounded_wait", "sfq_set_surrogate",
+            "sfq_table_pieces", "sfq_counters_check", "sfq_check_bounded_wait", "sfq_check_sqrt", "sfq_set_surrogate",
             "sfq_set_event_queue",
             "sfq_version"]
 
@@ -414,6 +416,16 @@ class Context:
         and adds 1 to counters' timeouts word (counters: a device counters_tensor)."""
         self._check(lib().sfq_check_bounded_wait(self._h, int(polls), _ptr(counters), _stream()),
                     "sfq_check_bounded_wait")
+
+    def check_sqrt(self, x):
+        """sfq_check_sqrt: the kernels' binary32 sqrt and 1/sqrt of the float32 device tensor x;
+        returns (sqrt, rsqrt)."""
+        import torch
+        if x.dtype != torch.float32 or not x.is_contiguous():
+            raise TypeError("x must be a contiguous float32 tensor")
+        so, ro = torch.empty_like(x), torch.empty_like(x)
+        self._check(lib().sfq_check_sqrt(self._h, x.numel(), _ptr(x), _ptr(so), _ptr(ro), _stream()), "sfq_check_sqrt")
+        return so, ro
 
 
 SORT_NOALLOC_MAX_N = 1 << 20
